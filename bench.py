@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark: block-decomposed int32 key sort on GB300 (Gkeys/s, % of HBM roofline).
+
+Workload (default): 2^28 uniform int32 keys from the seeded counter-based
+generator, split into p = 2 blocks (the paper's dual-core decomposition), sorted
+out of place through the C ABI (bs_sort_keys) on torch's current stream.
+One step = one whole sort: scatter bounds, tile-sort pass, in-block merge
+passes, cross-block merge round.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun) runs N independent replicas (each rank sorts its own
+array; weak scaling, no collective on the data path); timing is the max over
+ranks.  --impl reference times the CPU oracle (the paper's scatter / merge-sort
+/ merge-tree paradigm in plain C) on the host cores over a bounded sample.
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s and % HBM roofline, 2^28 int32 on 1 GB300"
+UNIT = "Gkeys/s"
+FALLBACK_HBM_GBS = 6800.0
+SEED = 0xB5EED000
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--p", type=int, default=2)
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
+    ap.add_argument("--tile-log2", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=26)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- environment helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    from paper_1105_6040_gb300 import build as b
+    return b._digest()
+
+
+def traffic_from_profiles(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` recorded under profiles/ by an ncu
+    capture of the current sources, or None when absent or stale."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    digest = source_digest()
+    pat = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+sources=(\w+)")
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, name)) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == kernel and m.group(2) == workload and m.group(4) == digest:
+                    return int(m.group(3))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if _num(r[1])]
+        mx = [float(r[2]) for r in rows if _num(r[2])]
+        power = [float(r[3]) for r in rows if _num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # "under load": the samples at the busy end of the distribution
+        load = [s for s in sm if s >= 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def _num(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_keys(args, rank: int):
+    from paper_1105_6040_gb300 import workloads as W
+    return W.int32_keys(args.dist, 1 << args.log2n, seed=SEED + rank)
+
+
+def workload_name(args) -> str:
+    return f"int32 key sort, 2^{args.log2n} {args.dist} keys, p={args.p} blocks"
+
+
+def config(args):
+    return {"workload": workload_name(args), "n": 1 << args.log2n, "p": args.p,
+            "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
+            "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
+            "stream": "torch current stream", "out_of_place": True}
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def oracle_rate(keys, repeats_s: float = 10.0, min_runs: int = 1):
+    """Time the CPU oracle on `keys` with one block and one thread per host core."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.load()
+    runs, t_total = 0, 0.0
+    while runs < min_runs or t_total < repeats_s:
+        t0 = time.perf_counter()
+        oracle.sort(keys, p=cores, threads=cores)
+        t_total += time.perf_counter() - t0
+        runs += 1
+    return keys.size * runs / t_total / 1e9, cores, runs, t_total
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1105_6040_gb300 import workloads as W
+    sample_log2 = min(args.log2n, 22)
+    keys = _first_keys(args, 1 << sample_log2)
+    cores = os.cpu_count() or 1
+    oracle.load()
+    for _ in range(args.warmup):
+        oracle.sort(keys, p=cores, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort(keys, p=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    value = keys.size * args.steps / dt / 1e9
+    sample = (f"first 2^{sample_log2} keys of the 2^{args.log2n}-key workload per step; "
+              f"oracle p={cores} blocks, {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _first_keys(args, count):
+    from paper_1105_6040_gb300 import workloads as W
+    if args.dist in ("uniform", "dup16"):
+        return W.int32_keys(args.dist, count, seed=SEED)  # counter-based: a prefix of the stream
+    full = W.int32_keys(args.dist, 1 << args.log2n, seed=SEED)
+    return full[:count].copy()
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1105_6040_gb300 import abi
+
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    if not torch.cuda.is_available():
+        raise SystemExit("no CUDA device: the benchmark measures the GPU path only")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = 1 << args.log2n
+    keys_h = make_keys(args, rank)
+    # the CPU baseline copy (a prefix of the same workload) is taken before any big GPU work
+    cpu_sample = keys_h[: 1 << min(args.cpu_sample_log2, args.log2n)].copy()
+
+    sorter = abi.Sorter(local, tile_log2=args.tile_log2)
+    d_in = torch.from_numpy(keys_h).cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step():
+        abi.bs_sort_keys(sorter.h, d_in.data_ptr(), d_out.data_ptr(), n, "int32", args.p, sp)
+
+    for _ in range(args.warmup):
+        step()
+    sorter.sync()
+    # correctness of the warm-up output (cheap property checks on the device)
+    assert bool((d_out[1:] >= d_out[:-1]).all()), "output not sorted"
+
+    # ---- timed region A: K whole sorts, CUDA events on the launching stream
+    abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    counts, _ = abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    launches = int(sum(counts.values()))
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * n * args.steps / (ms_max * 1e-3) / 1e9
+
+    # ---- timed region B: same steps with a CUDA event pair around every launch
+    kb = min(args.steps, 20)
+    abi.bs_launch_stats(sorter.h, reset=True)
+    sorter.set_timing(True)
+    barrier()
+    for _ in range(kb):
+        step()
+    barrier()
+    sorter.set_timing(False)
+    kms, kn = sorter.kernel_times()
+    kcounts, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
+    peak, peak_src = load_peak()
+    kernels = {}
+    for cls in ("tile_sort", "merge", "partition", "setup"):
+        if kn[cls]:
+            avg_ms = kms[cls] / kn[cls]
+            per_launch = kbytes[cls] / kn[cls]
+            kernels[cls] = {"launches_per_step": kn[cls] / kb, "ms_per_launch": avg_ms,
+                            "bytes_per_launch": per_launch,
+                            "gbs": per_launch / (avg_ms * 1e-3) / 1e9 if per_launch else None}
+    dom = max(("tile_sort", "merge"), key=lambda c: kms[c])
+    achieved = kernels[dom]["gbs"]
+    traffic = traffic_from_profiles("seg_merge_kernel" if dom == "merge" else "tile_sort_kernel",
+                                    f"int32_2e{args.log2n}_p{args.p}_{args.dist}")
+    passes = kernels["tile_sort"]["launches_per_step"] + kernels["merge"]["launches_per_step"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "merge pass" if dom == "merge" else "tile sort",
+                "peak_source": f"{peak_src} (copy bandwidth)",
+                "passes_per_step": passes,
+                "end_to_end_frac": passes * 2 * 4 * n / (ms_step * 1e-3) / 1e9 / peak}
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = torch.from_numpy(keys_h).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        for _ in range(2):
+            abi.bs_sort_keys_host(sorter.h, h_in.data_ptr(), h_out.data_ptr(), n, "int32", args.p)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            abi.bs_sort_keys_host(sorter.h, h_in.data_ptr(), h_out.data_ptr(), n, "int32", args.p)
+        dt = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+        assert np.all(h_out.numpy()[1:] >= h_out.numpy()[:-1])
+        e2e = {"value": world * n * args.e2e_steps / float(dt.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
+               "api": "bs_sort_keys_host (pinned host buffers)", "steps": args.e2e_steps}
+        del h_in, h_out
+
+    sorter.close()
+    del d_in, d_out
+    torch.cuda.empty_cache()
+
+    # ---- CPU baseline: the oracle on this host's cores, rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, runs, secs = oracle_rate(cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first 2^{min(args.cpu_sample_log2, args.log2n)} keys of the workload, "
+                         f"{runs} run(s) in {secs:.1f} s; oracle p={cores} blocks, {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "launches_per_step": launches / args.steps,
+            "clocks": clk, "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * bsort.h -- C ABI of the GB300 block-decomposed sort.
+ *
+ * The library sorts integer and floating-point key arrays that live in GPU
+ * memory, following the scatter / sort / merge paradigm of El-Nashar,
+ * "Parallel performance of MPI sorting algorithms on dual-core processor
+ * Windows-based systems" (IJDPS 2(3), 2011), Section 3.2 and Figure 1:
+ *   scatter (Fig. 1, steps 3-8)  the n keys are split into p blocks with
+ *                                bounds b_i = floor(i*n/p);
+ *   sort    (Fig. 1, step 9)     every block is sorted on its own -- here by
+ *                                CTA-local tile sorts and in-block merge
+ *                                passes in GPU memory;
+ *   merge   (Fig. 1, 10-22;      sorted blocks are merged pairwise, round
+ *            Sec. 3.2.2)         after round, into one nondecreasing output.
+ * The output does not depend on p; p only changes the schedule.
+ *
+ * Ordering.  Keys are ordered by an order-preserving unsigned code: signed
+ * integers by value, unsigned integers by value, floating point by the IEEE
+ * 754-2008 totalOrder predicate (Sec. 5.10): -NaN < -inf < ... < -0 < +0 <
+ * ... < +inf < +NaN, NaNs by payload.  Every comparison is an integer one, so
+ * results are bit-exact and deterministic.  Pair sorts are stable: equal keys
+ * keep their input order, and so do their values.
+ *
+ * Memory.  Every d_* pointer is a device pointer owned by the caller; the
+ * library never frees it.  Input and output may be the same buffer (in-place
+ * sort).  Scratch memory (a ping-pong copy of keys and values plus small
+ * index arrays, see bs_workspace_bytes) is owned by the handle and grown on
+ * demand with cudaMalloc; it is freed by bs_destroy.
+ *
+ * Streams and errors.  Calls are asynchronous on `stream` (a cudaStream_t
+ * passed as void*, NULL = the legacy default stream).  Argument errors are
+ * returned synchronously before anything is launched.  Errors the GPU finds
+ * (e.g. invalid segment offsets) are recorded in the handle and returned by
+ * bs_sync_status.  A handle is not thread safe: use one handle per host
+ * thread, and do not run two calls of one handle on different streams at the
+ * same time (they share the scratch memory).
+ */
+#ifndef BSORT_H
+#define BSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BS_OK = 0,
+    BS_ERR_INVALID_ARG = 1,       /* bad pointer, size, p, offsets */
+    BS_ERR_UNSUPPORTED_DTYPE = 2, /* key or value dtype not supported */
+    BS_ERR_OUT_OF_MEMORY = 3,     /* scratch allocation failed */
+    BS_ERR_CUDA = 4,              /* a CUDA runtime call or launch failed */
+    BS_ERR_TIMEOUT = 5            /* a bounded device-side wait gave up */
+} bs_status;
+
+typedef enum {
+    BS_NONE = -1, /* no values (keys-only) */
+    BS_INT32 = 0,
+    BS_UINT32 = 1,
+    BS_FLOAT32 = 2,
+    BS_INT64 = 3,
+    BS_UINT64 = 4,
+    BS_FLOAT64 = 5
+} bs_dtype;
+
+/* Kernel classes reported by the launch statistics. */
+typedef enum {
+    BS_KERNEL_TILE_SORT = 0, /* sort phase: CTA-local tile sort (1 pass) */
+    BS_KERNEL_MERGE = 1,     /* merge pass of sorted runs (1 pass each) */
+    BS_KERNEL_PARTITION = 2, /* merge-path split search per merge pass */
+    BS_KERNEL_SETUP = 3,     /* scatter bounds, tile map, offset checks */
+    BS_KERNEL_CLASSES = 4
+} bs_kernel_class;
+
+typedef struct bs_handle bs_handle;
+
+/*
+ * Create a handle on CUDA device `device` (the MPI_Init analogue of Fig. 1,
+ * step 1).  *h receives the handle.  Errors: INVALID_ARG (h NULL or no such
+ * device), CUDA, OUT_OF_MEMORY.
+ */
+bs_status bs_create(bs_handle **h, int device);
+
+/* Free the handle and its scratch memory (Fig. 1, step 23).  Waits for the
+ * handle's outstanding work.  NULL is accepted. */
+bs_status bs_destroy(bs_handle *h);
+
+/*
+ * Sort n keys of dtype kt from d_in into d_out (nondecreasing), decomposed
+ * into p blocks as in Fig. 1: each block sorted on its own, then the blocks
+ * merged pairwise (the merge phase).  p = 0 picks p = 1; p > n is clamped to
+ * n.  n = 0 is a no-op.  Key dtypes: all of bs_dtype except BS_NONE.
+ * Errors (synchronous): INVALID_ARG for n < 0, p < 0, a NULL pointer with
+ * n > 0; UNSUPPORTED_DTYPE; OUT_OF_MEMORY; CUDA.
+ */
+bs_status bs_sort_keys(bs_handle *h, const void *d_in, void *d_out, int64_t n,
+                       bs_dtype kt, int64_t p, void *stream);
+
+/*
+ * Stable sort of (key, value) pairs: keys d_kin -> d_kout as bs_sort_keys,
+ * and each value moves with its key (d_vin -> d_vout).  Values are any 4- or
+ * 8-byte type (vt gives the width; the bits are carried unchanged).  Equal
+ * keys keep their input order.  Errors as bs_sort_keys; vt == BS_NONE is
+ * UNSUPPORTED_DTYPE (use bs_sort_keys).
+ */
+bs_status bs_sort_pairs(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin,
+                        void *d_vout, int64_t n, bs_dtype kt, bs_dtype vt, int64_t p,
+                        void *stream);
+
+/*
+ * Batched sort: S independent segments of one key array are sorted in one
+ * call (the sort phase of Fig. 1 applied to every segment, no merge across
+ * segments).  Segment s is [d_offsets[s], d_offsets[s+1]); d_offsets is a
+ * device array of S+1 int64 with d_offsets[0] = 0, d_offsets[S] = n and
+ * nondecreasing entries (empty segments allowed).  d_vin / d_vout may be NULL
+ * (keys-only, vt = BS_NONE) or carry values (each segment sorted stably).
+ * max_seg_len: 0 = unknown, else an upper bound on every segment's length,
+ * which lets the library launch fewer merge passes.  Offsets that break these
+ * rules, or a segment longer than max_seg_len, are detected on the GPU and
+ * reported as INVALID_ARG by bs_sync_status; the output is then undefined but
+ * no memory outside the arrays is touched.
+ */
+bs_status bs_sort_segmented(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin,
+                            void *d_vout, int64_t n, const int64_t *d_offsets, int64_t S,
+                            int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream);
+
+/*
+ * Host-memory convenience: sort n keys from host buffer h_in into host
+ * buffer h_out (may be equal), copying through the handle's device buffers
+ * on the handle's internal stream; returns after the result is in h_out.
+ * Page-locked host buffers give the fastest copies.  Errors as bs_sort_keys.
+ */
+bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n,
+                            bs_dtype kt, int64_t p);
+
+/*
+ * Scratch bytes one sort of n keys (value type vt, BS_NONE for none) in S
+ * segments/blocks needs; the handle allocates this much on first use.
+ */
+bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes);
+
+/*
+ * Wait for the handle's last stream, then return the first error the GPU
+ * recorded since the previous call (and clear it), else a pending CUDA error,
+ * else BS_OK.
+ */
+bs_status bs_sync_status(bs_handle *h);
+
+/* Static string naming a status. */
+const char *bs_status_str(bs_status s);
+
+/*
+ * Launch statistics.  counts[k] (k < BS_KERNEL_CLASSES) receives the number
+ * of kernels of class k launched through this handle since creation or the
+ * last reset; `bytes[k]` the algorithmic bytes those launches had to move
+ * (every pass reads and writes each key and value once).  Either array may be
+ * NULL.  reset != 0 zeroes the counters afterwards.
+ */
+bs_status bs_launch_stats(bs_handle *h, int64_t *counts, double *bytes, int reset);
+
+/*
+ * Per-launch GPU timing.  With enable != 0 the handle records a CUDA event
+ * pair around every kernel it launches, on the launching stream.
+ * bs_kernel_times waits for those events and returns, per kernel class, the
+ * summed milliseconds (ms[k]) and the number of timed launches (n[k]); it
+ * then forgets the recorded events.
+ */
+bs_status bs_set_kernel_timing(bs_handle *h, int enable);
+bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n);
+
+/*
+ * Tuning: tile_log2 selects the tile size T = 2^tile_log2 keys of the sort
+ * phase and of the merge passes (supported: 11, 12, 13; 0 = default 12).
+ * Returns INVALID_ARG for an unsupported value.
+ */
+bs_status bs_set_tile_log2(bs_handle *h, int tile_log2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSORT_H */

@@ -1,0 +1,261 @@
+"""Thin Python binding of the C ABI in include/bsort.h (argument marshalling only).
+
+Every ``bs_*`` function here forwards to the function of the same name in
+``libbsort.so``; all sorting work runs in that library's CUDA kernels.  There is
+no CPU fallback: if the library cannot be loaded, or a call fails, an exception
+is raised.
+
+``Sorter`` wraps a handle and takes torch tensors (torch supplies device memory
+and streams only).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+BS_OK = 0
+BS_ERR_INVALID_ARG = 1
+BS_ERR_UNSUPPORTED_DTYPE = 2
+BS_ERR_OUT_OF_MEMORY = 3
+BS_ERR_CUDA = 4
+BS_ERR_TIMEOUT = 5
+
+DTYPES = {"none": -1, "int32": 0, "uint32": 1, "float32": 2, "int64": 3, "uint64": 4, "float64": 5}
+KERNEL_CLASSES = ("tile_sort", "merge", "partition", "setup")
+
+# every entry point include/bsort.h declares: name -> (argtypes, restype)
+_P, _I64, _INT = C.c_void_p, C.c_int64, C.c_int
+SIGNATURES = {
+    "bs_create": ([C.POINTER(C.c_void_p), _INT], _INT),
+    "bs_destroy": ([_P], _INT),
+    "bs_sort_keys": ([_P, _P, _P, _I64, _INT, _I64, _P], _INT),
+    "bs_sort_pairs": ([_P, _P, _P, _P, _P, _I64, _INT, _INT, _I64, _P], _INT),
+    "bs_sort_segmented": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT, _P], _INT),
+    "bs_sort_keys_host": ([_P, _P, _P, _I64, _INT, _I64], _INT),
+    "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
+    "bs_sync_status": ([_P], _INT),
+    "bs_status_str": ([_INT], C.c_char_p),
+    "bs_launch_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double), _INT], _INT),
+    "bs_set_kernel_timing": ([_P, _INT], _INT),
+    "bs_kernel_times": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], _INT),
+    "bs_set_tile_log2": ([_P, _INT], _INT),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class BsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libbsort.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libbsort.so not found at {path}; run the build first")
+            lib = C.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return load().bs_status_str(int(status)).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != BS_OK:
+        raise BsError(status, where)
+
+
+def dtype_code(dt) -> int:
+    """bs_dtype code of a dtype name, numpy dtype or torch dtype."""
+    if isinstance(dt, int):
+        return dt
+    name = str(dt).replace("torch.", "")
+    if name not in DTYPES:
+        raise BsError(BS_ERR_UNSUPPORTED_DTYPE, f"dtype {dt}")
+    return DTYPES[name]
+
+
+# ---------------------------------------------------------------- raw entry points
+
+
+def bs_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().bs_create(C.byref(h), int(device)), "bs_create")
+    return h.value
+
+
+def bs_destroy(h: int) -> None:
+    _check(load().bs_destroy(h), "bs_destroy")
+
+
+def bs_sort_keys(h, d_in, d_out, n, kt, p, stream=0) -> None:
+    _check(load().bs_sort_keys(h, d_in, d_out, int(n), dtype_code(kt), int(p), stream or None),
+           "bs_sort_keys")
+
+
+def bs_sort_pairs(h, d_kin, d_kout, d_vin, d_vout, n, kt, vt, p, stream=0) -> None:
+    _check(load().bs_sort_pairs(h, d_kin, d_kout, d_vin, d_vout, int(n), dtype_code(kt),
+                                dtype_code(vt), int(p), stream or None), "bs_sort_pairs")
+
+
+def bs_sort_segmented(h, d_kin, d_kout, d_vin, d_vout, n, d_offsets, S, max_seg_len, kt, vt,
+                      stream=0) -> None:
+    _check(load().bs_sort_segmented(h, d_kin, d_kout, d_vin, d_vout, int(n), d_offsets, int(S),
+                                    int(max_seg_len), dtype_code(kt), dtype_code(vt),
+                                    stream or None), "bs_sort_segmented")
+
+
+def bs_sort_keys_host(h, h_in, h_out, n, kt, p) -> None:
+    _check(load().bs_sort_keys_host(h, h_in, h_out, int(n), dtype_code(kt), int(p)),
+           "bs_sort_keys_host")
+
+
+def bs_workspace_bytes(n, S, kt, vt="none") -> int:
+    out = C.c_size_t()
+    _check(load().bs_workspace_bytes(int(n), int(S), dtype_code(kt), dtype_code(vt), C.byref(out)),
+           "bs_workspace_bytes")
+    return out.value
+
+
+def bs_sync_status(h) -> int:
+    return int(load().bs_sync_status(h))
+
+
+def bs_launch_stats(h, reset: bool = False, with_bytes: bool = True):
+    counts = (C.c_int64 * 4)()
+    byts = (C.c_double * 4)()
+    _check(load().bs_launch_stats(h, counts, byts if with_bytes else None, int(reset)),
+           "bs_launch_stats")
+    return ({k: counts[i] for i, k in enumerate(KERNEL_CLASSES)},
+            {k: byts[i] for i, k in enumerate(KERNEL_CLASSES)})
+
+
+def bs_set_kernel_timing(h, enable: bool) -> None:
+    _check(load().bs_set_kernel_timing(h, int(bool(enable))), "bs_set_kernel_timing")
+
+
+def bs_kernel_times(h):
+    ms = (C.c_double * 4)()
+    n = (C.c_int64 * 4)()
+    _check(load().bs_kernel_times(h, ms, n), "bs_kernel_times")
+    return ({k: ms[i] for i, k in enumerate(KERNEL_CLASSES)},
+            {k: n[i] for i, k in enumerate(KERNEL_CLASSES)})
+
+
+def bs_set_tile_log2(h, tile_log2: int) -> None:
+    _check(load().bs_set_tile_log2(h, int(tile_log2)), "bs_set_tile_log2")
+
+
+# ---------------------------------------------------------------- torch front end
+
+
+def _stream_ptr(stream, device) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return int(s.cuda_stream)
+
+
+class Sorter:
+    """A library handle on one CUDA device, taking torch tensors."""
+
+    def __init__(self, device=None, tile_log2: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Sorter needs a CUDA device; there is no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.h = bs_create(self.device.index)
+        if tile_log2:
+            bs_set_tile_log2(self.h, tile_log2)
+
+    def close(self):
+        if getattr(self, "h", None):
+            bs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t, name):
+        if not t.is_cuda or t.device != self.device or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous tensor on {self.device}")
+
+    def sort_keys(self, keys, out=None, p: int = 1, stream=None):
+        import torch
+        self._check_tensor(keys, "keys")
+        if out is None:
+            out = torch.empty_like(keys)
+        self._check_tensor(out, "out")
+        bs_sort_keys(self.h, keys.data_ptr(), out.data_ptr(), keys.numel(), keys.dtype, p,
+                     _stream_ptr(stream, self.device))
+        return out
+
+    def sort_pairs(self, keys, vals, kout=None, vout=None, p: int = 1, stream=None):
+        import torch
+        self._check_tensor(keys, "keys")
+        self._check_tensor(vals, "vals")
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        kout = torch.empty_like(keys) if kout is None else kout
+        vout = torch.empty_like(vals) if vout is None else vout
+        bs_sort_pairs(self.h, keys.data_ptr(), kout.data_ptr(), vals.data_ptr(), vout.data_ptr(),
+                      keys.numel(), keys.dtype, vals.dtype, p, _stream_ptr(stream, self.device))
+        return kout, vout
+
+    def sort_segmented(self, keys, offsets, vals=None, kout=None, vout=None,
+                       max_seg_len: int = 0, stream=None):
+        import torch
+        self._check_tensor(keys, "keys")
+        self._check_tensor(offsets, "offsets")
+        if offsets.dtype != torch.int64:
+            raise ValueError("offsets must be int64")
+        kout = torch.empty_like(keys) if kout is None else kout
+        if vals is not None:
+            self._check_tensor(vals, "vals")
+            vout = torch.empty_like(vals) if vout is None else vout
+        bs_sort_segmented(self.h, keys.data_ptr(), kout.data_ptr(),
+                          None if vals is None else vals.data_ptr(),
+                          None if vals is None else vout.data_ptr(),
+                          keys.numel(), offsets.data_ptr(), offsets.numel() - 1, max_seg_len,
+                          keys.dtype, "none" if vals is None else vals.dtype,
+                          _stream_ptr(stream, self.device))
+        return (kout, vout) if vals is not None else kout
+
+    def sort_keys_host(self, h_in, h_out=None, p: int = 1):
+        """Sort a host (CPU) tensor through the library's host-buffer entry point."""
+        import torch
+        if h_in.is_cuda or not h_in.is_contiguous():
+            raise ValueError("h_in must be a contiguous CPU tensor")
+        h_out = torch.empty_like(h_in) if h_out is None else h_out
+        bs_sort_keys_host(self.h, h_in.data_ptr(), h_out.data_ptr(), h_in.numel(), h_in.dtype, p)
+        return h_out
+
+    def sync(self) -> None:
+        _check(bs_sync_status(self.h), "bs_sync_status")
+
+    def stats(self, reset: bool = False):
+        return bs_launch_stats(self.h, reset=reset)
+
+    def set_timing(self, enable: bool) -> None:
+        bs_set_kernel_timing(self.h, enable)
+
+    def kernel_times(self):
+        return bs_kernel_times(self.h)

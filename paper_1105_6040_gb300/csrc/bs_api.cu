@@ -1,0 +1,626 @@
+// bs_api.cu -- C ABI, planner and set-up kernels of the block-decomposed sort.
+//
+// Planner (El-Nashar 2011, Fig. 1): for bs_sort_keys / bs_sort_pairs the p
+// blocks of the scatter phase are the balanced bounds b_i = floor(i*n/p)
+// (Fig. 1 steps 3-8), written to device memory by one small kernel; for
+// bs_sort_segmented the caller's offsets are the blocks.  Every block is cut
+// into tiles of T keys from its start; an exclusive scan of the per-block
+// tile counts gives each tile its block.  Then:
+//   sort phase   1 tile-sort pass + ceil(log2(tiles per block)) merge passes
+//   merge phase  ceil(log2 p) cross-block rounds (none for segmented sorts)
+// Buffers ping-pong between the caller's output and the scratch copy; each
+// block's tile sort writes to the buffer that makes its last pass land in the
+// output, so no copy pass is needed.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "bs_internal.h"
+
+using namespace bs;
+
+// ====================================================================== set-up kernels
+
+// Scatter bounds b_i = floor(i*n/p), i = 0..p (Fig. 1 steps 3-8).
+__global__ void balanced_offsets_kernel(int64_t *off, int64_t n, int64_t p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= p;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned __int128 v = (unsigned __int128)(uint64_t)i * (uint64_t)n;
+        off[i] = (int64_t)(v / (uint64_t)p);
+    }
+}
+
+// Caller offsets must start at 0, end at n, never decrease, and (when a
+// bound is given) hold no segment longer than max_len.
+__global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n, int64_t max_len,
+                                        int *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = off[i], hi = off[i + 1];
+        bool bad = hi < lo || lo < 0 || hi > n || (max_len > 0 && hi - lo > max_len);
+        if (i == 0 && lo != 0) bad = true;
+        if (i == S - 1 && hi != n) bad = true;
+        if (bad) atomicCAS(err, 0, (int)BS_ERR_INVALID_ARG);
+    }
+}
+
+constexpr int SCAN_TH = 256, SCAN_IT = 16, SCAN_BLOCK = SCAN_TH * SCAN_IT;
+
+__device__ __forceinline__ int64_t tiles_of(const int64_t *off, int64_t s, int64_t n, int logT) {
+    int64_t lo = clamp64(off[s], 0, n), hi = clamp64(off[s + 1], lo, n);
+    return (hi - lo + (int64_t(1) << logT) - 1) >> logT;
+}
+
+// Block-local inclusive scan of the per-segment tile counts.
+__global__ void __launch_bounds__(SCAN_TH)
+tile_scan_block_kernel(const int64_t *off, int64_t S, int64_t n, int logT, int64_t *tprefix,
+                       int64_t *bsum) {
+    __shared__ int64_t warp_tot[SCAN_TH / 32];
+    const int64_t base = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x * (int64_t)SCAN_IT;
+    int64_t v[SCAN_IT];
+    int64_t run = 0;
+#pragma unroll
+    for (int u = 0; u < SCAN_IT; ++u) {
+        int64_t i = base + u;
+        run += (i < S) ? tiles_of(off, i, n, logT) : 0;
+        v[u] = run;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    int64_t wprefix = 0;
+    for (int w = 0; w < wid; ++w) wprefix += warp_tot[w];
+    const int64_t excl = wprefix + x - run;
+#pragma unroll
+    for (int u = 0; u < SCAN_IT; ++u) {
+        int64_t i = base + u;
+        if (i < S) tprefix[i + 1] = excl + v[u];
+    }
+    if (threadIdx.x == SCAN_TH - 1) bsum[blockIdx.x] = excl + run;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tprefix[0] = 0;
+}
+
+// Exclusive scan of the block totals in place (one CTA, chunked with carry).
+__global__ void tile_scan_top_kernel(int64_t *bsum, int64_t nb) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+        int64_t i = c0 + threadIdx.x;
+        int64_t val = i < nb ? bsum[i] : 0;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int64_t x = val;
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        int64_t wprefix = 0;
+        for (int w = 0; w < wid; ++w) wprefix += warp_tot[w];
+        const int64_t base = carry;
+        if (i < nb) bsum[i] = base + wprefix + x - val;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = base + wprefix + x;
+        __syncthreads();
+    }
+}
+
+__global__ void tile_scan_add_kernel(int64_t *tprefix, const int64_t *bsum, int64_t S) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
+         i += (int64_t)gridDim.x * blockDim.x)
+        tprefix[i + 1] += bsum[i / SCAN_BLOCK];
+}
+
+// tseg[t] = the segment owning tile t (t < total tiles).
+__global__ void tile_map_kernel(const int64_t *tprefix, int64_t S, int32_t *tseg, int64_t ub) {
+    const int64_t total = tprefix[S];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ub && t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = S;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (tprefix[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        tseg[t] = (int32_t)lo;
+    }
+}
+
+// ====================================================================== handle
+
+struct bs_handle {
+    int device = 0;
+    int sms = 1;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_err = nullptr;
+    unsigned long long *d_counters = nullptr;
+    int64_t launches[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
+    int logT = 12;
+    cudaStream_t last_stream = nullptr;
+    // per-launch timing
+    bool timing = false;
+    struct Ev {
+        cudaEvent_t a, b;
+        int cls;
+    };
+    std::vector<Ev> evs;
+    std::vector<cudaEvent_t> spare;
+    // host-buffer entry point
+    cudaStream_t own_stream = nullptr;
+    void *hb = nullptr;
+    size_t hb_bytes = 0;
+};
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+cudaEvent_t take_event(bs_handle *h) {
+    if (!h->spare.empty()) {
+        cudaEvent_t e = h->spare.back();
+        h->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void launch_begin(void *owner, int cls, cudaStream_t s) {
+    bs_handle *h = (bs_handle *)owner;
+    if (!h->timing) return;
+    bs_handle::Ev ev{take_event(h), take_event(h), cls};
+    if (ev.a && ev.b) {
+        cudaEventRecord(ev.a, s);
+        h->evs.push_back(ev);
+    }
+}
+
+bool launch_end(void *owner, int cls, cudaStream_t s) {
+    bs_handle *h = (bs_handle *)owner;
+    if (cudaGetLastError() != cudaSuccess) return false;
+    h->launches[cls]++;
+    if (h->timing && !h->evs.empty() && h->evs.back().cls == cls) cudaEventRecord(h->evs.back().b, s);
+    return true;
+}
+
+struct WsLayout {
+    size_t tmp_k, tmp_v, off, tprefix, bsum, tseg, split, xs, total;
+};
+
+constexpr int64_t MIN_TILE = 2048;
+
+WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs) {
+    WsLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += (bytes + 255) & ~size_t(255);
+        return at;
+    };
+    const int64_t gt = (n + MIN_TILE - 1) / MIN_TILE;
+    const int64_t ub = gt + S + 1;
+    L.tmp_k = take((size_t)n * ks);
+    L.tmp_v = take((size_t)n * vs);
+    L.off = take((size_t)(S + 1) * 8);
+    L.tprefix = take((size_t)(S + 1) * 8);
+    L.bsum = take((size_t)((S + 1) / SCAN_BLOCK + 2) * 8);
+    L.tseg = take((size_t)ub * 4);
+    L.split = take((size_t)(ub + 1) * 8);
+    L.xs = take((size_t)(gt + 2) * sizeof(XSplit));
+    L.total = o;
+    return L;
+}
+
+bs_status ensure_ws(bs_handle *h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return BS_OK;
+    if (h->ws) {
+        cudaDeviceSynchronize();  // the old workspace may still be in use
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_OUT_OF_MEMORY;
+    }
+    h->ws_bytes = bytes;
+    return BS_OK;
+}
+
+int key_width(bs_dtype t) {
+    switch (t) {
+    case BS_INT32:
+    case BS_UINT32:
+    case BS_FLOAT32: return 4;
+    case BS_INT64:
+    case BS_UINT64:
+    case BS_FLOAT64: return 8;
+    default: return 0;
+    }
+}
+
+int key_codec(bs_dtype t) {
+    switch (t) {
+    case BS_INT32:
+    case BS_INT64: return CODEC_SIGNED;
+    case BS_FLOAT32:
+    case BS_FLOAT64: return CODEC_FLOAT;
+    default: return CODEC_IDENT;
+    }
+}
+
+int levels_for(int64_t len, int logT) {
+    if (len <= (int64_t(1) << logT)) return 0;
+    int64_t tiles = (len + (int64_t(1) << logT) - 1) >> logT;
+    int l = 0;
+    while ((int64_t(1) << l) < tiles) ++l;
+    return l;
+}
+
+int ceil_log2(int64_t p) {
+    int r = 0;
+    while ((int64_t(1) << r) < p) ++r;
+    return r;
+}
+
+inline unsigned blocks_for(int64_t work, int threads, int cap) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+// The whole method for one call.  balanced: blocks are floor(i*n/p); else
+// user_off holds S+1 segment offsets (no cross-block rounds).
+bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, void *vout, int64_t n,
+                  bs_dtype kt, int vbytes, bool balanced, int64_t p, const int64_t *user_off,
+                  int64_t S, int64_t max_len, cudaStream_t stream) {
+    const int kw = key_width(kt);
+    const int64_t blocks = balanced ? p : S;
+    if (blocks > INT32_MAX) return BS_ERR_INVALID_ARG;
+    const WsLayout W = ws_layout(n, blocks, (size_t)kw, (size_t)vbytes);
+    bs_status st = ensure_ws(h, W.total);
+    if (st != BS_OK) return st;
+    char *ws = (char *)h->ws;
+    h->last_stream = stream;
+
+    Geo g{};
+    g.S = blocks;
+    g.n = n;
+    g.logT = h->logT;
+    g.tprefix = (const int64_t *)(ws + W.tprefix);
+    g.tseg = (const int32_t *)(ws + W.tseg);
+    g.counters = h->d_counters;
+    g.R = balanced ? ceil_log2(p) : 0;
+
+    Launcher L{stream, h, h->sms, launch_begin, launch_end};
+    const int cap = h->sms * 8;
+    if (balanced) {
+        int64_t *off = (int64_t *)(ws + W.off);
+        launch_begin(h, CLS_SETUP, stream);
+        balanced_offsets_kernel<<<blocks_for(p + 1, 256, cap), 256, 0, stream>>>(off, n, p);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+        g.off = off;
+    } else {
+        launch_begin(h, CLS_SETUP, stream);
+        validate_offsets_kernel<<<blocks_for(S, 256, cap), 256, 0, stream>>>(user_off, S, n, max_len,
+                                                                            h->d_err);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+        g.off = user_off;
+    }
+
+    // tile map: exclusive scan of tiles per block, then tile -> block
+    int64_t *tprefix = (int64_t *)(ws + W.tprefix);
+    int64_t *bsum = (int64_t *)(ws + W.bsum);
+    const int64_t nsb = (blocks + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    launch_begin(h, CLS_SETUP, stream);
+    tile_scan_block_kernel<<<(unsigned)nsb, SCAN_TH, 0, stream>>>(g.off, blocks, n, g.logT, tprefix,
+                                                                  bsum);
+    if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    if (nsb > 1) {
+        launch_begin(h, CLS_SETUP, stream);
+        tile_scan_top_kernel<<<1, 1024, 0, stream>>>(bsum, nsb);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+        launch_begin(h, CLS_SETUP, stream);
+        tile_scan_add_kernel<<<blocks_for(blocks, 256, cap), 256, 0, stream>>>(tprefix, bsum, blocks);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    }
+    const int64_t T = int64_t(1) << g.logT;
+    const int64_t ub = (n + T - 1) / T + blocks;
+    g.ntiles_ub = ub;
+    launch_begin(h, CLS_SETUP, stream);
+    tile_map_kernel<<<blocks_for(ub, 256, cap), 256, 0, stream>>>(tprefix, blocks, (int32_t *)g.tseg, ub);
+    if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+
+    PassArgs a{};
+    a.g = g;  // g.ntiles_ub is set above, before the tile map launch
+    a.in_k = kin;
+    a.in_v = vin;
+    a.k0 = kout;
+    a.k1 = ws + W.tmp_k;
+    a.v0 = vout;
+    a.v1 = vbytes ? (void *)(ws + W.tmp_v) : nullptr;
+    a.codec = key_codec(kt);
+    a.vbytes = vbytes;
+    if (balanced) {
+        a.Lmax = levels_for((n + p - 1) / p, g.logT);
+    } else {
+        int64_t lim = (max_len > 0 && max_len < n) ? max_len : n;
+        a.Lmax = levels_for(lim, g.logT);
+    }
+    a.ntiles_ub = ub;
+    a.ntiles_total = tprefix + blocks;
+    a.split = (int64_t *)(ws + W.split);
+    a.xs = (XSplit *)(ws + W.xs);
+    return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
+}
+
+int value_width(bs_dtype vt) {
+    if (vt == BS_NONE) return 0;
+    return key_width(vt);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+bs_status bs_create(bs_handle **out, int device) {
+    if (!out) return BS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return BS_ERR_INVALID_ARG;
+    DevGuard dg(device);
+    bs_handle *h = new (std::nothrow) bs_handle();
+    if (!h) return BS_ERR_OUT_OF_MEMORY;
+    h->device = device;
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) h->sms = 1;
+    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->d_counters, sizeof(unsigned long long) * BS_KERNEL_CLASSES) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        bs_destroy(h);
+        return BS_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemset(h->d_err, 0, sizeof(int));
+    cudaMemset(h->d_counters, 0, sizeof(unsigned long long) * BS_KERNEL_CLASSES);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        bs_destroy(h);
+        return BS_ERR_CUDA;
+    }
+    *out = h;
+    return BS_OK;
+}
+
+bs_status bs_destroy(bs_handle *h) {
+    if (!h) return BS_OK;
+    DevGuard dg(h->device);
+    cudaDeviceSynchronize();
+    for (auto &e : h->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : h->spare) cudaEventDestroy(e);
+    if (h->ws) cudaFree(h->ws);
+    if (h->hb) cudaFree(h->hb);
+    if (h->d_err) cudaFree(h->d_err);
+    if (h->d_counters) cudaFree(h->d_counters);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return BS_OK;
+}
+
+bs_status bs_sort_keys(bs_handle *h, const void *d_in, void *d_out, int64_t n, bs_dtype kt, int64_t p,
+                       void *stream) {
+    if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0) return BS_OK;
+    if (!d_in || !d_out) return BS_ERR_INVALID_ARG;
+    if (p == 0) p = 1;
+    if (p > n) p = n;
+    DevGuard dg(h->device);
+    return do_sort(h, d_in, d_out, nullptr, nullptr, n, kt, 0, true, p, nullptr, p, 0,
+                   (cudaStream_t)stream);
+}
+
+bs_status bs_sort_pairs(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin, void *d_vout,
+                        int64_t n, bs_dtype kt, bs_dtype vt, int64_t p, void *stream) {
+    if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt) || !value_width(vt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0) return BS_OK;
+    if (!d_kin || !d_kout || !d_vin || !d_vout) return BS_ERR_INVALID_ARG;
+    if (p == 0) p = 1;
+    if (p > n) p = n;
+    DevGuard dg(h->device);
+    return do_sort(h, d_kin, d_kout, d_vin, d_vout, n, kt, value_width(vt), true, p, nullptr, p, 0,
+                   (cudaStream_t)stream);
+}
+
+bs_status bs_sort_segmented(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin,
+                            void *d_vout, int64_t n, const int64_t *d_offsets, int64_t S,
+                            int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream) {
+    if (!h || n < 0 || S < 0 || max_seg_len < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    const bool has_v = (vt != BS_NONE);
+    if (has_v && !value_width(vt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0 && S == 0) return BS_OK;
+    if (S == 0 || !d_offsets) return BS_ERR_INVALID_ARG;  // offsets must cover [0, n)
+    if (n > 0 && (!d_kin || !d_kout)) return BS_ERR_INVALID_ARG;
+    if (has_v && n > 0 && (!d_vin || !d_vout)) return BS_ERR_INVALID_ARG;
+    if (!has_v && (d_vin || d_vout)) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    if (n == 0) {
+        // still check the offsets (all must be 0)
+        h->last_stream = (cudaStream_t)stream;
+        launch_begin(h, CLS_SETUP, (cudaStream_t)stream);
+        validate_offsets_kernel<<<blocks_for(S, 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
+            d_offsets, S, 0, 0, h->d_err);
+        return launch_end(h, CLS_SETUP, (cudaStream_t)stream) ? BS_OK : BS_ERR_CUDA;
+    }
+    return do_sort(h, d_kin, d_kout, has_v ? d_vin : nullptr, has_v ? d_vout : nullptr, n, kt,
+                   has_v ? value_width(vt) : 0, false, 0, d_offsets, S, max_seg_len,
+                   (cudaStream_t)stream);
+}
+
+bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
+                            int64_t p) {
+    if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
+    const int kw = key_width(kt);
+    if (!kw) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0) return BS_OK;
+    if (!h_in || !h_out) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    const size_t bytes = (size_t)n * kw;
+    if (bytes > h->hb_bytes) {
+        if (h->hb) {
+            cudaStreamSynchronize(h->own_stream);
+            cudaFree(h->hb);
+            h->hb = nullptr;
+            h->hb_bytes = 0;
+        }
+        if (cudaMalloc(&h->hb, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return BS_ERR_OUT_OF_MEMORY;
+        }
+        h->hb_bytes = bytes;
+    }
+    cudaStream_t s = h->own_stream;
+    if (cudaMemcpyAsync(h->hb, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return BS_ERR_CUDA;
+    bs_status st = bs_sort_keys(h, h->hb, h->hb, n, kt, p, (void *)s);
+    if (st != BS_OK) return st;
+    if (cudaMemcpyAsync(h_out, h->hb, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return BS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BS_ERR_CUDA;
+    return BS_OK;
+}
+
+bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes) {
+    if (!bytes || n < 0 || S < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt) || (vt != BS_NONE && !value_width(vt))) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (S < 1) S = 1;
+    *bytes = ws_layout(n, S, (size_t)key_width(kt), (size_t)value_width(vt)).total;
+    return BS_OK;
+}
+
+bs_status bs_sync_status(bs_handle *h) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    int err = 0;
+    if (cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return BS_ERR_CUDA;
+    if (err) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return (bs_status)err;
+    }
+    if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
+    return BS_OK;
+}
+
+const char *bs_status_str(bs_status s) {
+    switch (s) {
+    case BS_OK: return "BS_OK";
+    case BS_ERR_INVALID_ARG: return "BS_ERR_INVALID_ARG";
+    case BS_ERR_UNSUPPORTED_DTYPE: return "BS_ERR_UNSUPPORTED_DTYPE";
+    case BS_ERR_OUT_OF_MEMORY: return "BS_ERR_OUT_OF_MEMORY";
+    case BS_ERR_CUDA: return "BS_ERR_CUDA";
+    case BS_ERR_TIMEOUT: return "BS_ERR_TIMEOUT";
+    default: return "BS_ERR_UNKNOWN";
+    }
+}
+
+bs_status bs_launch_stats(bs_handle *h, int64_t *counts, double *bytes, int reset) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    if (counts)
+        for (int k = 0; k < BS_KERNEL_CLASSES; ++k) counts[k] = h->launches[k];
+    if (bytes) {
+        unsigned long long c[BS_KERNEL_CLASSES];
+        if (cudaDeviceSynchronize() != cudaSuccess) return BS_ERR_CUDA;
+        if (cudaMemcpy(c, h->d_counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return BS_ERR_CUDA;
+        for (int k = 0; k < BS_KERNEL_CLASSES; ++k) bytes[k] = (double)c[k];
+    }
+    if (reset) {
+        for (int k = 0; k < BS_KERNEL_CLASSES; ++k) h->launches[k] = 0;
+        cudaDeviceSynchronize();
+        cudaMemset(h->d_counters, 0, sizeof(unsigned long long) * BS_KERNEL_CLASSES);
+        cudaDeviceSynchronize();
+    }
+    return BS_OK;
+}
+
+bs_status bs_set_kernel_timing(bs_handle *h, int enable) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return BS_OK;
+}
+
+bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    double acc[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
+    int64_t cnt[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
+    bs_status st = BS_OK;
+    for (auto &e : h->evs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(e.b) != cudaSuccess || cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) {
+            cudaGetLastError();
+            st = BS_ERR_CUDA;
+        } else {
+            acc[e.cls] += t;
+            cnt[e.cls] += 1;
+        }
+        h->spare.push_back(e.a);
+        h->spare.push_back(e.b);
+    }
+    h->evs.clear();
+    for (int k = 0; k < BS_KERNEL_CLASSES; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (n) n[k] = cnt[k];
+    }
+    return st;
+}
+
+bs_status bs_set_tile_log2(bs_handle *h, int tile_log2) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    if (tile_log2 == 0) tile_log2 = 12;
+    if (tile_log2 < 11 || tile_log2 > 13) return BS_ERR_INVALID_ARG;
+    h->logT = tile_log2;
+    return BS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// bs_passes.cuh -- host-side launch sequence of one sort (templated on the
+// key code type, value type and tile shape); instantiated per key width in
+// bs_u32.cu / bs_u64.cu.
+#pragma once
+
+#include <atomic>
+
+#include "bs_internal.h"
+
+namespace bs {
+
+template <class Kern> static int resident_ctas(Kern kern, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+template <class Kern> static bool allow_smem(Kern kern, size_t smem) {
+    if (smem <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+           cudaSuccess;
+}
+
+static inline int64_t grid_for(int64_t work, int64_t resident) {
+    int64_t g = work < resident ? work : resident;
+    return g < 1 ? 1 : g;
+}
+
+template <class K, class V, int THREADS, int KPT>
+bs_status run_passes_t(const PassArgs &a, Launcher &L) {
+    constexpr int T = THREADS * KPT;
+    const size_t smem = smem_bytes<K, V>(T);
+    auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
+    auto sm = seg_merge_kernel<K, V, THREADS, KPT>;
+    auto xm = xblock_merge_kernel<K, V, THREADS, KPT>;
+    auto sp = seg_partition_kernel<K>;
+    auto xp = x_partition_kernel<K>;
+    // per-instantiation launch shape, computed once (idempotent, so a race
+    // between host threads only repeats the same work)
+    static std::atomic<int> occ_ts{0}, occ_sm{0}, occ_xm{0};
+    if (!occ_ts.load()) {
+        if (!allow_smem(ts, smem) || !allow_smem(sm, smem) || !allow_smem(xm, smem)) return BS_ERR_CUDA;
+        occ_sm.store(resident_ctas(sm, THREADS, smem));
+        occ_xm.store(resident_ctas(xm, THREADS, smem));
+        occ_ts.store(resident_ctas(ts, THREADS, smem));
+    }
+    const Geo &g = a.g;
+    K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
+    V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
+    const int PT = 256;  // partition threads per CTA
+
+    // sort phase: every tile of every block
+    L.begin(L.owner, CLS_TILE_SORT, L.stream);
+    ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, smem, L.stream>>>(
+        g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
+    if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+
+    // sort phase, continued: in-block merge levels
+    for (int lv = 0; lv < a.Lmax; ++lv) {
+        L.begin(L.owner, CLS_PARTITION, L.stream);
+        sp<<<(unsigned)grid_for((a.ntiles_ub + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
+            g, lv, k0, k1, a.split, a.ntiles_total);
+        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return BS_ERR_CUDA;
+        L.begin(L.owner, CLS_MERGE, L.stream);
+        sm<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_sm), THREADS, smem, L.stream>>>(
+            g, lv, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+        if (!L.end(L.owner, CLS_MERGE, L.stream)) return BS_ERR_CUDA;
+    }
+
+    // merge phase: cross-block rounds on a global grid of output tiles
+    const int64_t gtiles = (g.n + T - 1) / T;
+    for (int r = 0; r < g.R; ++r) {
+        L.begin(L.owner, CLS_PARTITION, L.stream);
+        xp<<<(unsigned)grid_for((gtiles + 1 + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
+            g, r, k0, k1, a.xs, gtiles + 1);
+        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return BS_ERR_CUDA;
+        L.begin(L.owner, CLS_MERGE, L.stream);
+        xm<<<(unsigned)grid_for(gtiles, (int64_t)L.sms * occ_xm), THREADS, smem, L.stream>>>(
+            g, r, k0, k1, v0, v1, a.codec, a.xs, gtiles);
+        if (!L.end(L.owner, CLS_MERGE, L.stream)) return BS_ERR_CUDA;
+    }
+    return BS_OK;
+}
+
+// Dispatch on the value width and the tile shape (T = 2^logT = THREADS*16).
+template <class K, class V> bs_status run_passes_v(const PassArgs &a, Launcher &L) {
+    switch (a.g.logT) {
+    case 11: return run_passes_t<K, V, 128, 16>(a, L);
+    case 12: return run_passes_t<K, V, 256, 16>(a, L);
+    case 13: return run_passes_t<K, V, 512, 16>(a, L);
+    default: return BS_ERR_INVALID_ARG;
+    }
+}
+
+template <class K> bs_status run_passes_k(const PassArgs &a, Launcher &L) {
+    switch (a.vbytes) {
+    case 0: return run_passes_v<K, NoVal>(a, L);
+    case 4: return run_passes_v<K, uint32_t>(a, L);
+    case 8: return run_passes_v<K, uint64_t>(a, L);
+    default: return BS_ERR_UNSUPPORTED_DTYPE;
+    }
+}
+
+}  // namespace bs

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every entry point include/bsort.h
+declares; host-side argument checks answer without a GPU (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1105_6040_gb300 import abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "bsort.h")).read()
+    return sorted(set(re.findall(r"^(?:bs_status|const char \*)\s*(bs_\w+)\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for must in ("bs_create", "bs_destroy", "bs_sort_keys", "bs_sort_pairs", "bs_sort_segmented",
+                 "bs_workspace_bytes", "bs_sync_status", "bs_status_str"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = abi.load()
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+        assert name in abi.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings():
+    assert abi.status_str(abi.BS_OK) == "BS_OK"
+    assert abi.status_str(abi.BS_ERR_TIMEOUT) == "BS_ERR_TIMEOUT"
+    assert abi.status_str(99) == "BS_ERR_UNKNOWN"
+
+
+def test_null_handle_and_bad_args_rejected_synchronously():
+    lib = abi.load()
+    assert lib.bs_sort_keys(None, None, None, 10, 0, 1, None) == abi.BS_ERR_INVALID_ARG
+    assert lib.bs_sort_pairs(None, None, None, None, None, 10, 0, 0, 1, None) == abi.BS_ERR_INVALID_ARG
+    assert lib.bs_sort_segmented(None, None, None, None, None, 0, None, 0, 0, 0, -1, None) == \
+        abi.BS_ERR_INVALID_ARG
+    assert lib.bs_sync_status(None) == abi.BS_ERR_INVALID_ARG
+    assert lib.bs_create(None, 0) == abi.BS_ERR_INVALID_ARG
+    assert lib.bs_destroy(None) == abi.BS_OK
+    assert lib.bs_set_tile_log2(None, 12) == abi.BS_ERR_INVALID_ARG
+
+
+def test_workspace_bytes_is_host_only_and_grows_with_n():
+    a = abi.bs_workspace_bytes(1 << 20, 2, "int32")
+    b = abi.bs_workspace_bytes(1 << 22, 2, "int32")
+    c = abi.bs_workspace_bytes(1 << 20, 2, "uint64", "int32")
+    assert (1 << 22) <= a < b and c > a
+    with pytest.raises(abi.BsError):
+        abi.bs_workspace_bytes(-1, 1, "int32")
+    with pytest.raises(abi.BsError):
+        abi.bs_workspace_bytes(10, 1, "none")
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    st = abi.load().bs_create(C.byref(h), 0)
+    assert st in (abi.BS_ERR_CUDA, abi.BS_ERR_INVALID_ARG)
+    assert not h.value

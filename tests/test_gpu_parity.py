@@ -1,0 +1,306 @@
+"""CUDA path against the CPU oracle, bit for bit, through the C ABI (GPU only).
+
+Sorting has one correct output (keys-only) and one correct stable output
+(pairs), so every comparison here is exact: tolerance 0.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1105_6040_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+T = 4096  # default tile
+
+
+@pytest.fixture(scope="module")
+def sorter():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    yield s
+    s.close()
+
+
+def _bits(a: np.ndarray) -> np.ndarray:
+    return a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)
+
+
+def _to_dev(a: np.ndarray):
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).cuda().view(torch.uint32)
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda().view(torch.uint64)
+    return torch.from_numpy(a).cuda()
+
+
+def _to_host(t) -> np.ndarray:
+    if t.dtype == torch.uint32:
+        return t.view(torch.int32).cpu().numpy().view(np.uint32)
+    if t.dtype == torch.uint64:
+        return t.view(torch.int64).cpu().numpy().view(np.uint64)
+    return t.cpu().numpy()
+
+
+def gpu_keys(sorter, x, p):
+    out = sorter.sort_keys(_to_dev(x), p=p)
+    sorter.sync()
+    return _to_host(out)
+
+
+def check_keys(sorter, x, p):
+    got = gpu_keys(sorter, x, p)
+    want, _ = oracle.sort(x, p=p, threads=os.cpu_count() or 1)
+    assert np.array_equal(_bits(got), _bits(want)), (x.dtype, x.size, p)
+
+
+# ------------------------------------------------------------------ int32 keys, sizes x p
+
+SIZES = [1, 2, 3, 100, T - 1, T, T + 1, 3 * T + 17, 2 * T * 8 + 5, 65536 + 123]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("p", [1, 2, 3, 7, 64])
+def test_int32_uniform_sizes(sorter, n, p):
+    check_keys(sorter, W.uniform_int32(n, seed=n * 131 + p), p)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "reverse", "dup16"])
+@pytest.mark.parametrize("p", [1, 2, 5, 64, 4096])
+def test_int32_distributions_2e18(sorter, dist, p):
+    check_keys(sorter, W.int32_keys(dist, 1 << 18, seed=7), p)
+
+
+def test_pr1_config_2e20_p2(sorter):
+    """2^20 uniform int32 keys, p = 2 (the paper's dual-core decomposition)."""
+    check_keys(sorter, W.uniform_int32(1 << 20, seed=W.DEFAULT_SEED), 2)
+
+
+@pytest.mark.parametrize("n,p", [(1, 5), (7, 7), (10, 3), (5000, 5000), (5000, 6000), (9000, 4500)])
+def test_degenerate_blocks(sorter, n, p):
+    """p close to or above n: blocks of one or two keys (p > n clamps to n)."""
+    check_keys(sorter, W.uniform_int32(n, seed=3) % 97, p)
+
+
+def test_empty_is_noop(sorter):
+    x = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = sorter.sort_keys(x, p=3)
+    sorter.sync()
+    assert out.numel() == 0
+
+
+# ------------------------------------------------------------------ other key dtypes
+
+@pytest.mark.parametrize("maker", [
+    lambda n: W.uniform_int32(n, 11).view(np.uint32),
+    lambda n: W.normal_float32_edges(n, 12),
+    lambda n: W.uniform_float32_bits(n, 13),          # NaNs, infinities, subnormals
+    lambda n: W.uniform_uint64(n, 14).view(np.int64),
+    lambda n: W.uniform_uint64(n, 15),
+    lambda n: W.uniform_float64_bits(n, 16),
+    lambda n: W.zipf_uint64(n, 17),
+], ids=["uint32", "float32_normal_edges", "float32_bits", "int64", "uint64", "float64_bits",
+        "uint64_zipf"])
+@pytest.mark.parametrize("n,p", [(T + 3, 1), (50001, 3), (1 << 17, 16)])
+def test_key_dtypes(sorter, maker, n, p):
+    check_keys(sorter, maker(n), p)
+
+
+def test_float_total_order_specials(sorter):
+    words = [int(l.split()[0], 16) for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                               "float32_total_order.txt"))
+             if l.strip() and not l.startswith("#")]
+    w = np.array(words, dtype=np.uint32)
+    rng = np.random.default_rng(5)
+    x = np.tile(w, 300)[rng.permutation(300 * w.size)].view(np.float32)
+    got = gpu_keys(sorter, x, 4)
+    assert np.array_equal(_bits(got), np.repeat(w, 300))
+
+
+# ------------------------------------------------------------------ stable pairs
+
+@pytest.mark.parametrize("keys", ["uniform", "zipf", "dup"])
+@pytest.mark.parametrize("n,p", [(T - 1, 1), (3 * T + 5, 2), (1 << 18, 8), (100003, 7)])
+def test_pairs_uint64_index_payload_stable(sorter, keys, n, p):
+    k = {"uniform": lambda: W.uniform_uint64(n, 21), "zipf": lambda: W.zipf_uint64(n, 22),
+         "dup": lambda: W.uniform_uint64(n, 23) % np.uint64(5)}[keys]()
+    v = W.index_payload(n)
+    ko, vo = sorter.sort_pairs(_to_dev(k), _to_dev(v), p=p)
+    sorter.sync()
+    wk, wv = oracle.sort(k, v, p=p, threads=os.cpu_count() or 1)
+    assert np.array_equal(_to_host(ko), wk)
+    assert np.array_equal(_to_host(vo), wv)
+
+
+@pytest.mark.parametrize("kmaker,vdtype", [
+    (lambda n: W.uniform_int32(n, 31) % 1000, np.float32),
+    (lambda n: W.normal_float32_edges(n, 32), np.int64),
+    (lambda n: (W.uniform_uint64(n, 33) % np.uint64(77)).view(np.int64), np.int32),
+    (lambda n: W.uniform_float64_bits(n, 34), np.float64),
+], ids=["i32_f32", "f32_i64", "i64_i32", "f64_f64"])
+def test_pairs_mixed_dtypes(sorter, kmaker, vdtype):
+    n = 40000
+    k = kmaker(n)
+    v = W.uniform_uint64(n, 35).astype(np.uint64).view(np.int64)[:n].astype(vdtype) \
+        if vdtype != np.float64 else W.uniform_float64_bits(n, 36)
+    ko, vo = sorter.sort_pairs(_to_dev(k), _to_dev(v), p=3)
+    sorter.sync()
+    wk, wv = oracle.sort(k, v, p=3)
+    assert np.array_equal(_bits(_to_host(ko)), _bits(wk))
+    assert np.array_equal(_bits(_to_host(vo)), _bits(wv))
+
+
+# ------------------------------------------------------------------ segmented
+
+@pytest.mark.parametrize("with_vals", [False, True])
+@pytest.mark.parametrize("case", ["mixed", "tiny", "one", "with_empty", "loguniform"])
+def test_segmented(sorter, case, with_vals):
+    lens = {
+        "mixed": np.array([5, 0, T, T + 1, 1, 3 * T - 7, 17, 0, 9 * T + 3, 2]),
+        "tiny": np.full(3000, 3),
+        "one": np.array([100000]),
+        "with_empty": np.array([0, 0, 7, 0, 0, 0, T * 2, 0]),
+        "loguniform": W.loguniform_lengths(300, 16, 1 << 16, seed=41),
+    }[case].astype(np.int64)
+    off = W.offsets_from_lengths(lens)
+    n = int(off[-1])
+    k = W.uniform_int32(n, seed=42) % 5000
+    v = W.index_payload(n) if with_vals else None
+    res = sorter.sort_segmented(_to_dev(k), torch.from_numpy(off).cuda(),
+                                None if v is None else _to_dev(v))
+    sorter.sync()
+    wk, wv = oracle.sort_segmented(k, off, v)
+    if with_vals:
+        ko, vo = res
+        assert np.array_equal(_to_host(ko), wk) and np.array_equal(_to_host(vo), wv)
+    else:
+        assert np.array_equal(_to_host(res), wk)
+
+
+def test_segmented_max_len_hint(sorter):
+    lens = W.loguniform_lengths(500, 16, 1 << 14, seed=43)
+    off = W.offsets_from_lengths(lens)
+    k = W.uniform_int32(int(off[-1]), seed=44)
+    res = sorter.sort_segmented(_to_dev(k), torch.from_numpy(off).cuda(), max_seg_len=int(lens.max()))
+    sorter.sync()
+    assert np.array_equal(_to_host(res), oracle.sort_segmented(k, off)[0])
+
+
+def test_segmented_bad_offsets_reported_not_faulted(sorter):
+    from paper_1105_6040_gb300 import abi
+    k = _to_dev(W.uniform_int32(1000, 1))
+    for bad in ([0, 600, 400, 1000], [0, 500, 999], [5, 500, 1000], [0, 500, 2000]):
+        sorter.sort_segmented(k, torch.tensor(bad, dtype=torch.int64, device="cuda"))
+        assert abi.bs_sync_status(sorter.h) == abi.BS_ERR_INVALID_ARG
+    # a segment longer than the promised bound
+    sorter.sort_segmented(k, torch.tensor([0, 1000], dtype=torch.int64, device="cuda"), max_seg_len=10)
+    assert abi.bs_sync_status(sorter.h) == abi.BS_ERR_INVALID_ARG
+    sorter.sync()  # the handle is usable again
+
+
+# ------------------------------------------------------------------ in place, tiles, streams
+
+def test_in_place(sorter):
+    x = W.uniform_int32(3 * T + 11, 51)
+    t = _to_dev(x)
+    sorter.sort_keys(t, out=t, p=3)
+    sorter.sync()
+    assert np.array_equal(_to_host(t), np.sort(x))
+    k, v = W.uniform_uint64(20000, 52) % np.uint64(9), W.index_payload(20000)
+    tk, tv = _to_dev(k), _to_dev(v)
+    sorter.sort_pairs(tk, tv, kout=tk, vout=tv, p=2)
+    sorter.sync()
+    wk, wv = oracle.sort(k, v, p=2)
+    assert np.array_equal(_to_host(tk), wk) and np.array_equal(_to_host(tv), wv)
+
+
+@pytest.mark.parametrize("tile_log2", [11, 12, 13])
+def test_tile_shapes(tile_log2):
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0, tile_log2=tile_log2)
+    try:
+        for n, p in ((70001, 3), (1 << 17, 1)):
+            check_keys(s, W.uniform_int32(n, n + tile_log2), p)
+        k, v = W.zipf_uint64(30001, 61), W.index_payload(30001)
+        ko, vo = s.sort_pairs(_to_dev(k), _to_dev(v), p=5)
+        s.sync()
+        wk, wv = oracle.sort(k, v, p=5)
+        assert np.array_equal(_to_host(ko), wk) and np.array_equal(_to_host(vo), wv)
+    finally:
+        s.close()
+
+
+def test_side_stream(sorter):
+    x = W.uniform_int32(100000, 71)
+    t = _to_dev(x)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        out = sorter.sort_keys(t, p=4, stream=st)
+    st.synchronize()
+    assert np.array_equal(_to_host(out), np.sort(x))
+
+
+def test_host_buffer_entry_point(sorter):
+    x = W.uniform_int32(300001, 81)
+    h = torch.from_numpy(x).pin_memory()
+    out = sorter.sort_keys_host(h, p=2)
+    assert np.array_equal(out.numpy(), oracle.sort(x, p=2)[0])
+
+
+def test_invalid_args(sorter):
+    from paper_1105_6040_gb300 import abi
+    t = torch.zeros(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(abi.BsError) as e:
+        abi.bs_sort_keys(sorter.h, t.data_ptr(), t.data_ptr(), 10, "int32", -1)
+    assert e.value.status == abi.BS_ERR_INVALID_ARG
+    with pytest.raises(abi.BsError) as e:
+        abi.bs_sort_keys(sorter.h, t.data_ptr(), t.data_ptr(), 10, "none", 1)
+    assert e.value.status == abi.BS_ERR_UNSUPPORTED_DTYPE
+    with pytest.raises(abi.BsError) as e:
+        abi.bs_sort_pairs(sorter.h, t.data_ptr(), t.data_ptr(), t.data_ptr(), t.data_ptr(), 10,
+                          "int32", "none", 1)
+    assert e.value.status == abi.BS_ERR_UNSUPPORTED_DTYPE
+
+
+def test_launch_stats_count_passes(sorter):
+    sorter.stats(reset=True)
+    n = 1 << 20
+    sorter.sort_keys(_to_dev(W.uniform_int32(n, 91)), p=2)
+    counts, byts = sorter.stats(reset=True)
+    # 1 tile-sort pass + 7 in-block levels (2^19 / 4096 = 2^7 tiles) + 1 cross round
+    assert counts["tile_sort"] == 1 and counts["merge"] == 8
+    assert byts["tile_sort"] == 2 * 4 * n and byts["merge"] == 8 * 2 * 4 * n
+
+
+# ------------------------------------------------------------------ full sizes
+
+def test_2e26_int32_dup16_p4096_full_compare(sorter):
+    x = W.dup16_int32(1 << 26, seed=101)
+    check_keys(sorter, x, 4096)
+
+
+def test_2e28_int32_uniform_p2_sampled(sorter):
+    """The benchmark's workload: 2^28 uniform int32 keys, p = 2.  Checked by
+    properties that hold at any size plus sampled ranks computed by the oracle."""
+    n = 1 << 28
+    x = W.uniform_int32(n, seed=W.DEFAULT_SEED)
+    xt = _to_dev(x)
+    out = sorter.sort_keys(xt, p=2)
+    sorter.sync()
+    got = _to_host(out)
+    del xt, out
+    torch.cuda.empty_cache()
+    assert np.all(got[1:] >= got[:-1])                      # nondecreasing
+    cin, cout = oracle.encode(x), oracle.encode(got)
+    assert oracle.multiset_hash(cin, 0) == oracle.multiset_hash(cout, 0)  # permutation
+    assert oracle.multiset_hash(cin, 1) == oracle.multiset_hash(cout, 1)
+    rng = np.random.default_rng(0)
+    for k in np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 13)]):
+        lt, le = oracle.rank_bounds(cin, int(cout[k]))
+        assert lt <= k < le, k
