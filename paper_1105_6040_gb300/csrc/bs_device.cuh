@@ -127,98 +127,173 @@ __device__ __forceinline__ int64_t seg_of(const Geo &g, int64_t x) {
 
 // ---------------------------------------------------------------- merge path
 
-// Number of A items among the first `diag` outputs of the stable merge of
-// sorted A[0, na) and B[0, nb) (an A item wins a tie).  AccA/AccB index
-// shared or global memory.
-template <class K, class I, class AccA, class AccB>
-__device__ __forceinline__ I merge_path(AccA A, I na, AccB B, I nb, I diag) {
+// Number of A items among the first `diag` outputs of the merge of sorted
+// A[0, na) and B[0, nb), where b_less_a(ia, ib) says B[ib] goes strictly
+// before A[ia] (so an A item wins a tie and the merge is stable).
+template <class I, class BLessA>
+__device__ __forceinline__ I merge_path_pred(I na, I nb, I diag, BLessA b_less_a) {
     I lo = diag > nb ? diag - nb : I(0);
     I hi = diag < na ? diag : na;
     while (lo < hi) {
         I mid = (lo + hi) >> 1;
-        K a = A(mid), b = B(diag - 1 - mid);
-        if (!(b < a)) lo = mid + 1;
+        if (!b_less_a(mid, diag - 1 - mid)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
-// ---------------------------------------------------------------- in-register sorts
+// The same on plain codes through accessors A(i), B(i) (shared or global).
+template <class K, class I, class AccA, class AccB>
+__device__ __forceinline__ I merge_path(AccA A, I na, AccB B, I nb, I diag) {
+    return merge_path_pred<I>(na, nb, diag, [&](I ia, I ib) {
+        K a = A(ia), b = B(ib);
+        return b < a;
+    });
+}
 
-// Bitonic sorting network over N registers (keys only: no stability needed,
-// equal codes are identical bit patterns).
+// ---------------------------------------------------------------- in-register networks
+
+// Keys with a tie-breaking index: (code, index) pairs are all distinct, so
+// any network sorts them into one order, and it is the stable order when the
+// index follows the input order.
+template <class K> __device__ __forceinline__ bool ki_less(K ak, uint32_t ai, K bk, uint32_t bi) {
+    return ak < bk || (ak == bk && ai < bi);
+}
+
+template <class K> __device__ __forceinline__ void cas_keys(K &a, K &b) {
+    K lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+template <class K>
+__device__ __forceinline__ void cas_pairs(K &a, uint32_t &ai, K &b, uint32_t &bi) {
+    const bool sw = ki_less(b, bi, a, ai);
+    const K k = a;
+    const uint32_t i = ai;
+    a = sw ? b : a;
+    ai = sw ? bi : ai;
+    b = sw ? k : b;
+    bi = sw ? i : bi;
+}
+
+// Bitonic sorting network over N registers, ascending (Batcher 1968).
 template <int N, class K> __device__ __forceinline__ void reg_sort_keys(K (&k)[N]) {
 #pragma unroll
-    for (int size = 2; size <= N; size <<= 1) {
+    for (int size = 2; size <= N; size <<= 1)
 #pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 const int j = i ^ stride;
                 if (j > i) {
-                    K x = k[i], y = k[j];
-                    K lo = x < y ? x : y, hi = x < y ? y : x;
-                    if ((i & size) == 0) k[i] = lo, k[j] = hi;
-                    else k[i] = hi, k[j] = lo;
+                    if ((i & size) == 0) cas_keys(k[i], k[j]);
+                    else cas_keys(k[j], k[i]);
                 }
             }
-        }
-    }
 }
 
-// Odd-even transposition network: exchanges only adjacent registers on a
-// strict '>', so equal keys keep their order (stable; used for pairs).
-template <int N, class K, class V>
-__device__ __forceinline__ void reg_sort_pairs(K (&k)[N], V (&v)[N]) {
+template <int N, class K> __device__ __forceinline__ void reg_sort_pairs(K (&k)[N], uint32_t (&x)[N]) {
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
+    for (int size = 2; size <= N; size <<= 1)
 #pragma unroll
-        for (int i = r & 1; i + 1 < N; i += 2) {
-            bool sw = k[i + 1] < k[i];
-            K ka = k[i], kb = k[i + 1];
-            V va = v[i], vb = v[i + 1];
-            k[i] = sw ? kb : ka;
-            k[i + 1] = sw ? ka : kb;
-            v[i] = sw ? vb : va;
-            v[i + 1] = sw ? va : vb;
-        }
-    }
-}
-
-// ---------------------------------------------------------------- CTA-level merge
-
-// Merge VT outputs starting at diagonal `diag` of lists A = sk[a0, a0+na) and
-// B = sk[b0, b0+nb) held in shared memory (padded indices).  Writes the
-// codes to out[] and the shared index of each output to idx[].
-template <class K, int VT>
-__device__ __forceinline__ void serial_merge(const K *sk, int a0, int na, int b0, int nb, int i,
-                                             int j, int count, K (&out)[VT], int (&idx)[VT]) {
-    K a = i < na ? sk[spad<K>(a0 + i)] : K(0);
-    K b = j < nb ? sk[spad<K>(b0 + j)] : K(0);
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
 #pragma unroll
-    for (int v = 0; v < VT; ++v) {
-        if (v < count) {
-            bool take_a = (j >= nb) || (i < na && !(b < a));
-            out[v] = take_a ? a : b;
-            idx[v] = take_a ? a0 + i : b0 + j;
-            if (take_a) {
-                ++i;
-                if (i < na) a = sk[spad<K>(a0 + i)];
-            } else {
-                ++j;
-                if (j < nb) b = sk[spad<K>(b0 + j)];
+            for (int i = 0; i < N; ++i) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    if ((i & size) == 0) cas_pairs(k[i], x[i], k[j], x[j]);
+                    else cas_pairs(k[j], x[j], k[i], x[i]);
+                }
             }
-        }
+}
+
+// Ascending bitonic merge of a bitonic sequence held in N registers.
+template <int N, class K> __device__ __forceinline__ void bitonic_merge_keys(K (&k)[N]) {
+#pragma unroll
+    for (int s = N >> 1; s > 0; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & s) == 0) cas_keys(k[i], k[i + s]);
+}
+
+template <int N, class K>
+__device__ __forceinline__ void bitonic_merge_pairs(K (&k)[N], uint32_t (&x)[N]) {
+#pragma unroll
+    for (int s = N >> 1; s > 0; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & s) == 0) cas_pairs(k[i], x[i], k[i + s], x[i + s]);
+}
+
+// ---------------------------------------------------------------- candidate merge
+
+// The VT smallest items of the merge of sorted lists A = S[a0, a0+na) and
+// B = S[b0, b0+nb) in shared memory (padded indices), from the merge-path
+// split (i, j).  With A' = A[i, i+VT) and B' = B[j, j+VT), the sequence
+// A' ++ reverse(B') is bitonic; one half-cleaner step (min of A'[u] and
+// B'[VT-1-u]) keeps its VT smallest items and a bitonic merge sorts them
+// (Batcher's bitonic merger).  The 2*VT shared loads are independent of one
+// another, so no load waits on a comparison.  Items past a list end read as
+// the largest code, so they never displace a real item.
+template <class K, int VT>
+__device__ __forceinline__ void cand_merge_keys(const K *sk, int a0, int na, int b0, int nb, int i,
+                                                int j, K (&out)[VT]) {
+#pragma unroll
+    for (int u = 0; u < VT; ++u) {
+        const int ia = i + u, ib = j + VT - 1 - u;
+        const K x = ia < na ? sk[spad<K>(a0 + ia)] : max_code<K>();
+        const K y = ib < nb ? sk[spad<K>(b0 + ib)] : max_code<K>();
+        out[u] = x < y ? x : y;
     }
+    bitonic_merge_keys<VT>(out);
+}
+
+// Pairs: each item carries a tie-breaking index -- sx[position] when sx is
+// given (original input positions), else the shared-memory position itself
+// (A before B, each in input order).  Missing items are (largest code,
+// largest index).  oi[] receives the indices of the outputs.
+template <class K, int VT>
+__device__ __forceinline__ void cand_merge_pairs(const K *sk, const uint32_t *sx, int a0, int na,
+                                                 int b0, int nb, int i, int j, K (&out)[VT],
+                                                 uint32_t (&oi)[VT]) {
+#pragma unroll
+    for (int u = 0; u < VT; ++u) {
+        const int ia = i + u, ib = j + VT - 1 - u;
+        K x = max_code<K>(), y = max_code<K>();
+        uint32_t xi = 0xffffffffu, yi = 0xffffffffu;
+        if (ia < na) {
+            x = sk[spad<K>(a0 + ia)];
+            xi = sx ? sx[spad<uint32_t>(a0 + ia)] : (uint32_t)(a0 + ia);
+        }
+        if (ib < nb) {
+            y = sk[spad<K>(b0 + ib)];
+            yi = sx ? sx[spad<uint32_t>(b0 + ib)] : (uint32_t)(b0 + ib);
+        }
+        const bool tx = ki_less(x, xi, y, yi);
+        out[u] = tx ? x : y;
+        oi[u] = tx ? xi : yi;
+    }
+    bitonic_merge_pairs<VT>(out, oi);
 }
 
 // ---------------------------------------------------------------- tile sort
 
+// Shared memory of the tile sort: codes, then (pairs) original positions and
+// values, each at a 16-byte boundary.
+template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
+    return smem_val_offset<K>(T) +
+           (sizeof(V) > 1 ? smem_val_offset<uint32_t>(T) + sizeof(V) * (size_t)spad_size<V>(T) : 0);
+}
+
 // Tile sort (the sort phase of Fig. 1 step 9 at CTA scale).  Tile t covers
-// keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e); it is sorted with
-// an in-register network per thread (KPT keys) and log2(THREADS) rounds of
-// shared-memory merge-path merges, then written -- decoded if this is the
-// last pass for the segment -- to the buffer its merge schedule starts from.
+// keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
+// KPT keys in registers, then log2(THREADS) rounds merge pairs of sorted
+// lists through shared memory (merge-path split + candidate merge); rounds
+// whose lists live inside one warp synchronise only that warp.  Pairs sort
+// (code, original position), which is the stable order; values move once,
+// at the final store.  The sorted tile is written -- decoded if this is the
+// segment's last pass -- to the buffer its merge schedule starts from.
 template <class K, class V, int THREADS, int KPT>
 __global__ void __launch_bounds__(THREADS)
 tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
@@ -228,7 +303,8 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
     constexpr bool HV = HasVal<V>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
-    V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(T));
+    uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw + smem_val_offset<K>(T));
+    V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(T) + smem_val_offset<uint32_t>(T));
 
     const int64_t total = min(*ntiles_total, g.ntiles_ub);
     const int tid = threadIdx.x;
@@ -245,83 +321,65 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
         K *dst_k = par ? buf_k1 : buf_k0;
         V *dst_v = par ? buf_v1 : buf_v0;
 
+        // striped, coalesced load; padding slots get the largest code (and,
+        // for pairs, positions past every real one)
         K k[KPT];
-        V v[KPT];
-        int idx[KPT];
-        if constexpr (!HV) {
-            // striped load (coalesced); any arrangement is fine for keys only
+        uint32_t x[KPT];
 #pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                int x = tid + u * THREADS;
-                k[u] = x < cnt ? enc_code(in_k[base + x], codec) : max_code<K>();
+        for (int u = 0; u < KPT; ++u) {
+            const int pos = tid + u * THREADS;
+            k[u] = pos < cnt ? enc_code(in_k[base + pos], codec) : max_code<K>();
+            if constexpr (HV) {
+                x[u] = (uint32_t)pos;
+                if (pos < cnt) sv[spad<V>(pos)] = in_v[base + pos];
             }
-        } else {
-            // pairs: blocked arrangement (thread tid holds tile positions
-            // tid*KPT .. tid*KPT+KPT-1) through shared memory, so that the
-            // stable network and merges see keys in input order.
-#pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                int x = tid + u * THREADS;
-                if (x < cnt) {
-                    k[u] = enc_code(in_k[base + x], codec);
-                    v[u] = in_v[base + x];
-                } else {
-                    k[u] = max_code<K>();
-                }
-                sk[spad<K>(x)] = k[u];
-                sv[spad<V>(x)] = v[u];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                k[u] = sk[spad<K>(tid * KPT + u)];
-                v[u] = sv[spad<V>(tid * KPT + u)];
-            }
-            __syncthreads();
         }
+        if constexpr (HV) reg_sort_pairs<KPT>(k, x);
+        else reg_sort_keys<KPT>(k);
 
-        if constexpr (!HV) reg_sort_keys<KPT>(k);
-        else reg_sort_pairs<KPT>(k, v);
-
-        // merge rounds: lists of m = KPT << r keys, pairs of lists merged
 #pragma unroll 1
         for (int r = 0; (KPT << r) < T; ++r) {
+            const bool warp_round = (2 << r) <= 32;  // both lists inside one warp
 #pragma unroll
             for (int u = 0; u < KPT; ++u) {
                 sk[spad<K>(tid * KPT + u)] = k[u];
-                if constexpr (HV) sv[spad<V>(tid * KPT + u)] = v[u];
+                if constexpr (HV) sx[spad<uint32_t>(tid * KPT + u)] = x[u];
             }
-            __syncthreads();
+            if (warp_round) __syncwarp();
+            else __syncthreads();
             const int m = KPT << r;
-            const int grp = tid >> (r + 1);
-            const int rank = tid & ((1 << (r + 1)) - 1);
-            const int a0 = grp * 2 * m, b0 = a0 + m;
-            const int diag = rank * KPT;
-            auto A = [&](int i) { return sk[spad<K>(a0 + i)]; };
-            auto B = [&](int i) { return sk[spad<K>(b0 + i)]; };
-            int i = merge_path<K, int>(A, m, B, m, diag);
-            serial_merge<K, KPT>(sk, a0, m, b0, m, i, diag - i, KPT, k, idx);
+            const int a0 = (tid >> (r + 1)) * 2 * m, b0 = a0 + m;
+            const int diag = (tid & ((2 << r) - 1)) * KPT;
             if constexpr (HV) {
-#pragma unroll
-                for (int u = 0; u < KPT; ++u) v[u] = sv[spad<V>(idx[u])];
+                const int i = merge_path_pred<int>(m, m, diag, [&](int ia, int ib) {
+                    return ki_less(sk[spad<K>(b0 + ib)], sx[spad<uint32_t>(b0 + ib)],
+                                   sk[spad<K>(a0 + ia)], sx[spad<uint32_t>(a0 + ia)]);
+                });
+                cand_merge_pairs<K, KPT>(sk, sx, a0, m, b0, m, i, diag - i, k, x);
+            } else {
+                const int i = merge_path_pred<int>(m, m, diag, [&](int ia, int ib) {
+                    return sk[spad<K>(b0 + ib)] < sk[spad<K>(a0 + ia)];
+                });
+                cand_merge_keys<K, KPT>(sk, a0, m, b0, m, i, diag - i, k);
             }
-            __syncthreads();
+            if (warp_round) __syncwarp();
+            else __syncthreads();
         }
 
         // blocked registers -> shared -> coalesced striped store
 #pragma unroll
         for (int u = 0; u < KPT; ++u) {
             sk[spad<K>(tid * KPT + u)] = k[u];
-            if constexpr (HV) sv[spad<V>(tid * KPT + u)] = v[u];
+            if constexpr (HV) sx[spad<uint32_t>(tid * KPT + u)] = x[u];
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < KPT; ++u) {
-            int x = tid + u * THREADS;
-            if (x < cnt) {
-                K c = sk[spad<K>(x)];
-                dst_k[base + x] = fin ? dec_code(c, codec) : c;
-                if constexpr (HV) dst_v[base + x] = sv[spad<V>(x)];
+            const int pos = tid + u * THREADS;
+            if (pos < cnt) {
+                const K c = sk[spad<K>(pos)];
+                dst_k[base + pos] = fin ? dec_code(c, codec) : c;
+                if constexpr (HV) dst_v[base + pos] = sv[spad<V>((int)sx[spad<uint32_t>(pos)])];
             }
         }
         if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * cnt);
@@ -343,7 +401,7 @@ __device__ __forceinline__ void cta_merge(const K *__restrict__ src_k, const V *
     const int total = na + nb;
     K k[VT];
     V v[VT];
-    int idx[VT];
+    uint32_t idx[VT];
 #pragma unroll
     for (int u = 0; u < VT; ++u) {
         int x = tid + u * THREADS;
@@ -363,15 +421,18 @@ __device__ __forceinline__ void cta_merge(const K *__restrict__ src_k, const V *
     }
     __syncthreads();
     const int diag = min(tid * VT, total);
-    auto A = [&](int i) { return sk[spad<K>(i)]; };
-    auto B = [&](int i) { return sk[spad<K>(na + i)]; };
-    const int i = merge_path<K, int>(A, na, B, nb, diag);
+    // shared positions order A before B, so "ties to A" is the stable order
+    const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) {
+        return sk[spad<K>(na + ib)] < sk[spad<K>(ia)];
+    });
     const int count = min(VT, total - diag);
-    serial_merge<K, VT>(sk, 0, na, na, nb, i, diag - i, count, k, idx);
     if constexpr (HV) {
+        cand_merge_pairs<K, VT>(sk, nullptr, 0, na, na, nb, i, diag - i, k, idx);
 #pragma unroll
         for (int u = 0; u < VT; ++u)
-            if (u < count) v[u] = sv[spad<V>(idx[u])];
+            if (u < count) v[u] = sv[spad<V>((int)idx[u])];
+    } else {
+        cand_merge_keys<K, VT>(sk, 0, na, na, nb, i, diag - i, k);
     }
     __syncthreads();
 #pragma unroll

@@ -31,6 +31,7 @@ template <class K, class V, int THREADS, int KPT>
 bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     constexpr int T = THREADS * KPT;
     const size_t smem = smem_bytes<K, V>(T);
+    const size_t tsmem = tile_smem_bytes<K, V>(T);
     auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
     auto sm = seg_merge_kernel<K, V, THREADS, KPT>;
     auto xm = xblock_merge_kernel<K, V, THREADS, KPT>;
@@ -40,10 +41,10 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     // between host threads only repeats the same work)
     static std::atomic<int> occ_ts{0}, occ_sm{0}, occ_xm{0};
     if (!occ_ts.load()) {
-        if (!allow_smem(ts, smem) || !allow_smem(sm, smem) || !allow_smem(xm, smem)) return BS_ERR_CUDA;
+        if (!allow_smem(ts, tsmem) || !allow_smem(sm, smem) || !allow_smem(xm, smem)) return BS_ERR_CUDA;
         occ_sm.store(resident_ctas(sm, THREADS, smem));
         occ_xm.store(resident_ctas(xm, THREADS, smem));
-        occ_ts.store(resident_ctas(ts, THREADS, smem));
+        occ_ts.store(resident_ctas(ts, THREADS, tsmem));
     }
     const Geo &g = a.g;
     K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
@@ -52,7 +53,7 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
 
     // sort phase: every tile of every block
     L.begin(L.owner, CLS_TILE_SORT, L.stream);
-    ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, smem, L.stream>>>(
+    ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem, L.stream>>>(
         g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
     if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
 
