@@ -51,7 +51,8 @@ typedef enum {
     BS_ERR_UNSUPPORTED_DTYPE = 2, /* key or value dtype not supported */
     BS_ERR_OUT_OF_MEMORY = 3,     /* scratch allocation failed */
     BS_ERR_CUDA = 4,              /* a CUDA runtime call or launch failed */
-    BS_ERR_TIMEOUT = 5            /* a bounded device-side wait gave up */
+    BS_ERR_TIMEOUT = 5,           /* a bounded device-side wait gave up */
+    BS_ERR_TOO_LARGE = 6          /* request exceeds a fixed capacity (bs_sort_keys_noalloc) */
 } bs_status;
 
 typedef enum {
@@ -175,6 +176,36 @@ bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n);
  * Returns INVALID_ARG for an unsupported value.
  */
 bs_status bs_set_tile_log2(bs_handle *h, int tile_log2);
+
+/*
+ * bs_sort_keys_noalloc -- the paper has no counterpart; this is a service
+ * for callers that must not allocate GPU memory while they sort (a latency-
+ * critical path where cudaMalloc/cudaFree could stall the device, a plug-in
+ * whose host framework owns all device memory, a fixed start-up budget).
+ *
+ * It sorts like bs_sort_keys (same passes, same bit-exact output) but takes
+ * no handle and allocates nothing: its scratch is one fixed array compiled
+ * into the library, BS_NOALLOC_MAX_KEY_BYTES plus 64 KiB, which every GPU that
+ * loads the library holds until the process exits.  The caller still passes
+ * the input and output buffers (device pointers, may be equal).
+ *
+ * Limits: n * sizeof(key) <= BS_NOALLOC_MAX_KEY_BYTES (2^20 four-byte keys or
+ * 2^19 eight-byte keys) and p <= BS_NOALLOC_MAX_BLOCKS after clamping (p = 0
+ * means 1, p > n means n).  Larger requests return BS_ERR_TOO_LARGE before
+ * any GPU work.  Other errors: INVALID_ARG (n < 0, p < 0, NULL pointer with
+ * n > 0), UNSUPPORTED_DTYPE, CUDA (a launch failed).
+ *
+ * It runs on the calling thread's current CUDA device, asynchronously on
+ * `stream`.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls whose GPU work overlaps in
+ * time (other streams or host threads on the same device) race and corrupt
+ * each other's output, so serialise them.
+ */
+#define BS_NOALLOC_MAX_KEY_BYTES (4u << 20)
+#define BS_NOALLOC_MAX_BLOCKS 1024
+bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t n, bs_dtype kt, int64_t p,
+                               void *stream);
 
 #ifdef __cplusplus
 }

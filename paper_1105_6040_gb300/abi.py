@@ -22,6 +22,7 @@ BS_ERR_UNSUPPORTED_DTYPE = 2
 BS_ERR_OUT_OF_MEMORY = 3
 BS_ERR_CUDA = 4
 BS_ERR_TIMEOUT = 5
+BS_ERR_TOO_LARGE = 6
 
 DTYPES = {"none": -1, "int32": 0, "uint32": 1, "float32": 2, "int64": 3, "uint64": 4, "float64": 5}
 KERNEL_CLASSES = ("tile_sort", "merge", "partition", "setup")
@@ -42,6 +43,7 @@ SIGNATURES = {
     "bs_set_kernel_timing": ([_P, _INT], _INT),
     "bs_kernel_times": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], _INT),
     "bs_set_tile_log2": ([_P, _INT], _INT),
+    "bs_sort_keys_noalloc": ([_P, _P, _I64, _INT, _I64, _P], _INT),
 }
 
 _lib = None
@@ -159,6 +161,15 @@ def bs_kernel_times(h):
 
 def bs_set_tile_log2(h, tile_log2: int) -> None:
     _check(load().bs_set_tile_log2(h, int(tile_log2)), "bs_set_tile_log2")
+
+
+def bs_sort_keys_noalloc(d_in, d_out, n, kt, p, stream=0) -> None:
+    """Key sort for callers that must not allocate GPU memory while sorting:
+    the library's fixed scratch array is used instead of a handle's memory
+    (at most 4 MiB of keys, p <= 1024; larger requests raise BS_ERR_TOO_LARGE).
+    Calls share that array, so calls overlapping on the GPU must be avoided."""
+    _check(load().bs_sort_keys_noalloc(d_in, d_out, int(n), dtype_code(kt), int(p), stream or None),
+           "bs_sort_keys_noalloc")
 
 
 # ---------------------------------------------------------------- torch front end

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_NAME = "libbsort.so"
-UNITS = ["bs_api.cu", "bs_u32.cu", "bs_u64.cu"]
+UNITS = ["bs_api.cu", "bs_u32.cu", "bs_u64.cu", "bs_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

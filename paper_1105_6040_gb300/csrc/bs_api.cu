@@ -558,6 +558,7 @@ const char *bs_status_str(bs_status s) {
     case BS_ERR_OUT_OF_MEMORY: return "BS_ERR_OUT_OF_MEMORY";
     case BS_ERR_CUDA: return "BS_ERR_CUDA";
     case BS_ERR_TIMEOUT: return "BS_ERR_TIMEOUT";
+    case BS_ERR_TOO_LARGE: return "BS_ERR_TOO_LARGE";
     default: return "BS_ERR_UNKNOWN";
     }
 }
