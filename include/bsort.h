@@ -5,12 +5,12 @@
  * memory, following the scatter / sort / merge paradigm of El-Nashar,
  * "Parallel performance of MPI sorting algorithms on dual-core processor
  * Windows-based systems" (IJDPS 2(3), 2011), Section 3.2 and Figure 1:
- *   scatter (Fig. 1, steps 3-8)  the n keys are split into p blocks with
+ *   scatter (Fig. 1)             the n keys are split into p blocks with
  *                                bounds b_i = floor(i*n/p);
- *   sort    (Fig. 1, step 9)     every block is sorted on its own -- here by
+ *   sort    (Fig. 1)             every block is sorted on its own -- here by
  *                                CTA-local tile sorts and in-block merge
  *                                passes in GPU memory;
- *   merge   (Fig. 1, 10-22;      sorted blocks are merged pairwise, round
+ *   merge   (Fig. 1;             sorted blocks are merged pairwise, round
  *            Sec. 3.2.2)         after round, into one nondecreasing output.
  * The output does not depend on p; p only changes the schedule.
  *
@@ -77,13 +77,13 @@ typedef enum {
 typedef struct bs_handle bs_handle;
 
 /*
- * Create a handle on CUDA device `device` (the MPI_Init analogue of Fig. 1,
- * step 1).  *h receives the handle.  Errors: INVALID_ARG (h NULL or no such
+ * Create a handle on CUDA device `device` (the analogue of initialising MPI
+ * in Fig. 1).  *h receives the handle.  Errors: INVALID_ARG (h NULL or no such
  * device), CUDA, OUT_OF_MEMORY.
  */
 bs_status bs_create(bs_handle **h, int device);
 
-/* Free the handle and its scratch memory (Fig. 1, step 23).  Waits for the
+/* Free the handle and its scratch memory (finalising MPI in Fig. 1).  Waits for the
  * handle's outstanding work.  NULL is accepted. */
 bs_status bs_destroy(bs_handle *h);
 

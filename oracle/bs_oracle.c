@@ -147,7 +147,7 @@ int orc_decode(const uint64_t *codes, int dtype, int64_t n, void *keys) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Scatter phase (Fig. 1 steps 3-8): block i holds items [b_i, b_{i+1}).     */
+/* Scatter phase (Fig. 1): block i holds items [b_i, b_{i+1}).              */
 /* ------------------------------------------------------------------------ */
 
 int orc_block_bounds(int64_t n, int64_t p, int64_t *bounds) {
@@ -379,7 +379,7 @@ static void merge_tree(recs r, recs tmp, const int64_t *bounds, int64_t p, int t
 }
 
 /*
- * Odd-even compare-split (the reading of Fig. 1, steps 10-22).  The paper's
+ * Odd-even compare-split (the reading of Fig. 1's merge phase).  The paper's
  * partition size s = n/p assumes equal blocks; p alternating rounds sort p
  * equal blocks, but not unequal ones (n = 4, p = 3 is a counterexample).  So
  * every block gets the capacity s = ceil(n/p): its items, then +infinity

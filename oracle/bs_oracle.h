@@ -8,13 +8,13 @@
  * What it computes: the scatter / sort / merge paradigm of El-Nashar (IJDPS
  * 2011), Section 3.2 and Figure 1, applied to records (code, payload):
  *   1. scatter: the n items are split into p blocks with balanced bounds
- *      b_i = floor(i*n/p)                                  (Fig. 1, steps 3-8)
+ *      b_i = floor(i*n/p)                        (Fig. 1, scatter phase)
  *   2. sort phase: every block is sorted by one of the paper's sequential
  *      sorts -- top-down merge sort (Fig. 3), bubble sort (Fig. 2) or
- *      quick sort (Fig. 4)                                  (Fig. 1, step 9)
+ *      quick sort (Fig. 4)                        (Fig. 1, sort phase)
  *   3. merge phase: sorted blocks are merged into one list, in one of three
  *      forms: a pairwise merge tree, the odd-even compare-split exchange read
- *      from Fig. 1 steps 10-22, or the gather-to-master fold of Section 3.2.2.
+ *      from Fig. 1's merge phase, or the gather-to-master fold of Section 3.2.2.
  * Keys are ordered by an order-preserving unsigned code (IEEE 754-2008
  * totalOrder for floating point), so every comparison is an integer one.
  *

@@ -2,7 +2,7 @@
 //
 // Planner (El-Nashar 2011, Fig. 1): for bs_sort_keys / bs_sort_pairs the p
 // blocks of the scatter phase are the balanced bounds b_i = floor(i*n/p)
-// (Fig. 1 steps 3-8), written to device memory by one small kernel; for
+// (Fig. 1, scatter phase), written to device memory by one small kernel; for
 // bs_sort_segmented the caller's offsets are the blocks.  Every block is cut
 // into tiles of T keys from its start; an exclusive scan of the per-block
 // tile counts gives each tile its block.  Then:
@@ -26,7 +26,7 @@ using namespace bs;
 
 // ====================================================================== set-up kernels
 
-// Scatter bounds b_i = floor(i*n/p), i = 0..p (Fig. 1 steps 3-8).
+// Scatter bounds b_i = floor(i*n/p), i = 0..p (Fig. 1, scatter phase).
 __global__ void balanced_offsets_kernel(int64_t *off, int64_t n, int64_t p) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= p;
          i += (int64_t)gridDim.x * blockDim.x) {

@@ -1,14 +1,14 @@
 // bs_device.cuh -- device code of the GB300 block-decomposed sort.
 //
 // The paper's paradigm (El-Nashar 2011, Sec. 3.2, Fig. 1) mapped to one GPU:
-//   scatter (Fig. 1 steps 3-8): block bounds are an offsets array in device
+//   scatter (Fig. 1, scatter phase): block bounds are an offsets array in device
 //     memory; nothing moves.
-//   sort phase (Fig. 1 step 9): every block is cut into tiles of T keys
+//   sort phase (Fig. 1): every block is cut into tiles of T keys
 //     aligned to the block start; one CTA sorts one tile in registers and
 //     shared memory (tile_sort_kernel), then merge passes in HBM join the
 //     sorted tiles of each block pairwise (seg_merge_kernel) until the block
 //     is one sorted run.
-//   merge phase (Fig. 1 steps 10-22): pairs of sorted blocks are merged,
+//   merge phase (Fig. 1): pairs of sorted blocks are merged,
 //     round after round (xblock_merge_kernel), until one run remains.
 // Every merge pass splits its output into tiles of T keys; the start of each
 // output tile inside its pair of runs is found by a merge-path search
@@ -286,7 +286,7 @@ template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes
            (sizeof(V) > 1 ? smem_val_offset<uint32_t>(T) + sizeof(V) * (size_t)spad_size<V>(T) : 0);
 }
 
-// Tile sort (the sort phase of Fig. 1 step 9 at CTA scale).  Tile t covers
+// Tile sort (the sort phase of Fig. 1 at CTA scale).  Tile t covers
 // keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
 // KPT keys in registers, then log2(THREADS) rounds merge pairs of sorted
 // lists through shared memory (merge-path split + candidate merge); rounds
