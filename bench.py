@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
     ap.add_argument("--tile-log2", type=int, default=12)
+    ap.add_argument("--merge", choices=["auto", "simple", "tma"], default="auto",
+                    help="merge-pass kernel (auto: TMA pipeline where it fits)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
@@ -170,6 +172,7 @@ def workload_name(args) -> str:
 def config(args):
     return {"workload": workload_name(args), "n": 1 << args.log2n, "p": args.p,
             "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
+            "merge_kernel": args.merge,
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
             "stream": "torch current stream", "out_of_place": True}
 
@@ -257,7 +260,7 @@ def run_ours(args):
     # the CPU baseline copy (a prefix of the same workload) is taken before any big GPU work
     cpu_sample = keys_h[: 1 << min(args.cpu_sample_log2, args.log2n)].copy()
 
-    sorter = abi.Sorter(local, tile_log2=args.tile_log2)
+    sorter = abi.Sorter(local, tile_log2=args.tile_log2, merge_kernel=args.merge)
     d_in = torch.from_numpy(keys_h).cuda()
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()

@@ -177,6 +177,21 @@ bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n);
  */
 bs_status bs_set_tile_log2(bs_handle *h, int tile_log2);
 
+/* Options of bs_set_option. */
+typedef enum {
+    BS_OPT_TILE_LOG2 = 0,    /* value: 11, 12 or 13 (0 = default 12), as bs_set_tile_log2 */
+    BS_OPT_MERGE_KERNEL = 1  /* value: a bs_merge_kernel */
+} bs_option;
+
+/* Merge-pass kernels.  AUTO uses the TMA pipeline when the tile's stages fit
+ * two CTAs per SM and every buffer is 16-byte aligned; TMA uses it whenever
+ * it fits (still falling back on misaligned buffers); SIMPLE never. */
+typedef enum { BS_MERGE_AUTO = 0, BS_MERGE_SIMPLE = 1, BS_MERGE_TMA = 2 } bs_merge_kernel;
+
+/* Set one tuning option of the handle; INVALID_ARG for an unknown option or
+ * an unsupported value.  Results never depend on options, only speed does. */
+bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value);
+
 /*
  * bs_sort_keys_noalloc -- the paper has no counterpart; this is a service
  * for callers that must not allocate GPU memory while they sort (a latency-

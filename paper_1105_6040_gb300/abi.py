@@ -43,6 +43,7 @@ SIGNATURES = {
     "bs_set_kernel_timing": ([_P, _INT], _INT),
     "bs_kernel_times": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], _INT),
     "bs_set_tile_log2": ([_P, _INT], _INT),
+    "bs_set_option": ([_P, _INT, _I64], _INT),
     "bs_sort_keys_noalloc": ([_P, _P, _I64, _INT, _I64, _P], _INT),
 }
 
@@ -163,6 +164,18 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
     _check(load().bs_set_tile_log2(h, int(tile_log2)), "bs_set_tile_log2")
 
 
+OPTIONS = {"tile_log2": 0, "merge_kernel": 1}
+MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}
+
+
+def bs_set_option(h, option, value) -> None:
+    if isinstance(option, str):
+        option = OPTIONS[option]
+    if isinstance(value, str):
+        value = MERGE_KERNELS[value]
+    _check(load().bs_set_option(h, int(option), int(value)), "bs_set_option")
+
+
 def bs_sort_keys_noalloc(d_in, d_out, n, kt, p, stream=0) -> None:
     """Key sort for callers that must not allocate GPU memory while sorting:
     the library's fixed scratch array is used instead of a handle's memory
@@ -184,7 +197,7 @@ def _stream_ptr(stream, device) -> int:
 class Sorter:
     """A library handle on one CUDA device, taking torch tensors."""
 
-    def __init__(self, device=None, tile_log2: int = 0):
+    def __init__(self, device=None, tile_log2: int = 0, merge_kernel: str = "auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Sorter needs a CUDA device; there is no CPU path")
@@ -193,6 +206,8 @@ class Sorter:
         self.h = bs_create(self.device.index)
         if tile_log2:
             bs_set_tile_log2(self.h, tile_log2)
+        if merge_kernel != "auto":
+            bs_set_option(self.h, "merge_kernel", merge_kernel)
 
     def close(self):
         if getattr(self, "h", None):

@@ -150,6 +150,7 @@ struct bs_handle {
     unsigned long long *d_counters = nullptr;
     int64_t launches[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
     int logT = 12;
+    int merge_impl = MERGE_AUTO;
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -208,7 +209,7 @@ bool launch_end(void *owner, int cls, cudaStream_t s) {
 }
 
 struct WsLayout {
-    size_t tmp_k, tmp_v, off, tprefix, bsum, tseg, split, xs, total;
+    size_t tmp_k, tmp_v, off, tprefix, bsum, tseg, split, total;
 };
 
 constexpr int64_t MIN_TILE = 2048;
@@ -228,9 +229,9 @@ WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs) {
     L.off = take((size_t)(S + 1) * 8);
     L.tprefix = take((size_t)(S + 1) * 8);
     L.bsum = take((size_t)((S + 1) / SCAN_BLOCK + 2) * 8);
+    const int64_t xt = xblock_tiles_max(n, S, 11);
     L.tseg = take((size_t)ub * 4);
-    L.split = take((size_t)(ub + 1) * 8);
-    L.xs = take((size_t)(gt + 2) * sizeof(XSplit));
+    L.split = take((size_t)((ub > xt ? ub : xt) + 1) * 8);
     L.total = o;
     return L;
 }
@@ -315,6 +316,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     g.tprefix = (const int64_t *)(ws + W.tprefix);
     g.tseg = (const int32_t *)(ws + W.tseg);
     g.counters = h->d_counters;
+    g.err = h->d_err;
     g.R = balanced ? ceil_log2(p) : 0;
 
     Launcher L{stream, h, h->sms, launch_begin, launch_end};
@@ -375,7 +377,8 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.ntiles_ub = ub;
     a.ntiles_total = tprefix + blocks;
     a.split = (int64_t *)(ws + W.split);
-    a.xs = (XSplit *)(ws + W.xs);
+    const uintptr_t al = (uintptr_t)kout | (uintptr_t)a.k1 | (uintptr_t)vout | (uintptr_t)a.v1;
+    a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -614,6 +617,20 @@ bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n) {
         if (n) n[k] = cnt[k];
     }
     return st;
+}
+
+bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
+    if (!h) return BS_ERR_INVALID_ARG;
+    switch (opt) {
+    case BS_OPT_TILE_LOG2:
+        return bs_set_tile_log2(h, (int)value);
+    case BS_OPT_MERGE_KERNEL:
+        if (value < BS_MERGE_AUTO || value > BS_MERGE_TMA) return BS_ERR_INVALID_ARG;
+        h->merge_impl = (int)value;
+        return BS_OK;
+    default:
+        return BS_ERR_INVALID_ARG;
+    }
 }
 
 bs_status bs_set_tile_log2(bs_handle *h, int tile_log2) {

@@ -24,6 +24,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bsort.h"
+
 namespace bs {
 
 // ---------------------------------------------------------------- key codes
@@ -90,6 +92,7 @@ struct Geo {
     int logT;                // tile = 2^logT keys
     int R;                   // number of cross-block merge rounds
     unsigned long long *counters;  // algorithmic bytes per kernel class (stats)
+    int *err;                      // device status flag (nullable): first error wins
 };
 
 // kernel classes of the statistics counters (same order as the C ABI's)
@@ -301,7 +304,7 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
                  const int64_t *__restrict__ ntiles_total) {
     constexpr int T = THREADS * KPT;
     constexpr bool HV = HasVal<V>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
     uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw + smem_val_offset<K>(T));
     V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(T) + smem_val_offset<uint32_t>(T));
@@ -455,75 +458,119 @@ __device__ __forceinline__ void cta_merge(const K *__restrict__ src_k, const V *
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- in-segment merge level
+// ---------------------------------------------------------------- merge levels
 
-// Level L of the in-block merge schedule: inside segment [s, e) the runs are
-// [s + q*W, s + (q+1)*W) with W = T << L; runs 2c and 2c+1 merge into one.
-// A segment is active at level L while L < its level count.  The pair holding
-// tile t of the segment and the buffer parities follow from (s, e, L).
-struct SegPair {
+// One merge pass.  kind LEVEL_SEG: level `lv` of the in-block schedule --
+// inside segment [s, e) the runs are [s + q*W, s + (q+1)*W), W = T << lv, and
+// runs 2c, 2c+1 merge into one; a segment is active while lv < its level
+// count.  kind LEVEL_XBLOCK: round `r` of the merge phase -- groups of 2^r
+// consecutive blocks are runs and pair k merges groups 2k and 2k+1 (an
+// unpaired last group is copied).  Every pair is cut into output tiles of T
+// keys from its start (tpp tiles per pair for cross-block rounds, enough for
+// the longest pair; tiles past a pair's end are inactive), so an output tile
+// always lies inside one pair.
+enum : int { LEVEL_SEG = 0, LEVEL_XBLOCK = 1 };
+struct Level {
+    int kind;
+    int lv;          // LEVEL_SEG: level
+    int r;           // LEVEL_XBLOCK: round
+    int64_t tpp;     // LEVEL_XBLOCK: tiles per pair
+    int64_t ntiles;  // LEVEL_XBLOCK: npairs * tpp (LEVEL_SEG reads the tile count)
+};
+
+struct TilePair {
     int64_t ps, pm, pe;  // A = [ps, pm), B = [pm, pe)
     int64_t x0, x1;      // this tile's output range
     int src, dst;        // buffer parities
     bool fin, active;
 };
 
-__device__ __forceinline__ SegPair seg_pair(const Geo &g, int64_t t, int level) {
-    SegPair p;
-    const int64_t s = g.tseg[t];
-    int64_t slo, shi;
-    seg_bounds(g, s, slo, shi);
-    const int Ls = seg_levels(shi - slo, g.logT);
-    p.active = level < Ls;
-    const int64_t j = t - g.tprefix[s];
-    p.x0 = slo + (j << g.logT);
-    p.x1 = min(p.x0 + (int64_t(1) << g.logT), shi);
-    const int64_t W = int64_t(1) << (g.logT + level);
-    const int64_t cell = (j << g.logT) / (2 * W);
-    p.ps = slo + cell * 2 * W;
-    p.pm = min(p.ps + W, shi);
-    p.pe = min(p.ps + 2 * W, shi);
-    p.src = (Ls - level + g.R) & 1;
-    p.dst = (Ls - level - 1 + g.R) & 1;
-    p.fin = (level == Ls - 1) && g.R == 0;
+__device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int64_t t) {
+    TilePair p;
+    const int64_t T = int64_t(1) << g.logT;
+    if (L.kind == LEVEL_SEG) {
+        const int64_t s = g.tseg[t];
+        int64_t slo, shi;
+        seg_bounds(g, s, slo, shi);
+        const int Ls = seg_levels(shi - slo, g.logT);
+        const int64_t j = t - g.tprefix[s];
+        const int64_t W = T << L.lv;
+        p.active = L.lv < Ls;
+        p.x0 = slo + j * T;
+        p.x1 = min(p.x0 + T, shi);
+        p.ps = slo + (j >> (L.lv + 1)) * 2 * W;
+        p.pm = min(p.ps + W, shi);
+        p.pe = min(p.ps + 2 * W, shi);
+        p.src = (Ls - L.lv + g.R) & 1;
+        p.dst = (Ls - L.lv - 1 + g.R) & 1;
+        p.fin = (L.lv == Ls - 1) && g.R == 0;
+    } else {
+        const int64_t k = t / L.tpp, j = t - k * L.tpp;
+        const int64_t G = int64_t(2) << L.r, H = int64_t(1) << L.r;
+        p.ps = clamp64(g.off[min(k * G, g.S)], 0, g.n);
+        p.pm = clamp64(g.off[min(k * G + H, g.S)], p.ps, g.n);
+        p.pe = clamp64(g.off[min(k * G + G, g.S)], p.pm, g.n);
+        p.x0 = p.ps + j * T;
+        p.x1 = min(p.x0 + T, p.pe);
+        p.active = p.x0 < p.pe;
+        p.src = (g.R - L.r) & 1;
+        p.dst = (g.R - L.r - 1) & 1;
+        p.fin = (L.r == g.R - 1);
+    }
     return p;
+}
+
+__device__ __forceinline__ int64_t level_tiles(const Geo &g, const Level &L,
+                                               const int64_t *ntiles_total) {
+    return L.kind == LEVEL_SEG ? min(*ntiles_total, g.ntiles_ub) : L.ntiles;
 }
 
 // Merge-path split (absolute A index) at the start of every active tile.
 template <class K>
-__global__ void seg_partition_kernel(Geo g, int level, const K *buf0, const K *buf1,
-                                     int64_t *split, const int64_t *__restrict__ ntiles_total) {
-    const int64_t total = min(*ntiles_total, g.ntiles_ub);
+__global__ void partition_kernel(Geo g, Level L, const K *buf0, const K *buf1, int64_t *split,
+                                 const int64_t *__restrict__ ntiles_total) {
+    const int64_t total = level_tiles(g, L, ntiles_total);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        SegPair p = seg_pair(g, t, level);
+        const TilePair p = tile_pair(g, L, t);
         if (!p.active) continue;
         const K *src = p.src ? buf1 : buf0;
-        const int64_t na = p.pm - p.ps, nb = p.pe - p.pm;
         auto A = [&](int64_t i) { return src[p.ps + i]; };
         auto B = [&](int64_t i) { return src[p.pm + i]; };
-        split[t] = p.ps + merge_path<K, int64_t>(A, na, B, nb, p.x0 - p.ps);
+        split[t] = p.ps + merge_path<K, int64_t>(A, p.pm - p.ps, B, p.pe - p.pm, p.x0 - p.ps);
     }
 }
 
+// The A and B slices of tile t: A[a_lo, a_hi), B[b_lo, b_hi) -> out[x0, x1).
+struct Slice {
+    int64_t a_lo, a_hi, b_lo, b_hi;
+};
+__device__ __forceinline__ Slice tile_slice(const TilePair &p, const int64_t *split, int64_t t) {
+    Slice q;
+    q.a_lo = split[t];
+    q.a_hi = (p.x1 == p.pe) ? p.pm : split[t + 1];
+    q.b_lo = p.pm + (p.x0 - p.ps) - (q.a_lo - p.ps);
+    q.b_hi = p.pm + (p.x1 - p.ps) - (q.a_hi - p.ps);
+    return q;
+}
+
+// Merge pass staged through padded shared memory with plain loads (any key
+// and value type, any alignment).
 template <class K, class V, int THREADS, int VT>
 __global__ void __launch_bounds__(THREADS)
-seg_merge_kernel(Geo g, int level, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
-                 const int64_t *__restrict__ split, const int64_t *__restrict__ ntiles_total) {
+merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
+             const int64_t *__restrict__ split, const int64_t *__restrict__ ntiles_total) {
     constexpr int TT = THREADS * VT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
     V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(TT));
-    const int64_t total = min(*ntiles_total, g.ntiles_ub);
+    const int64_t total = level_tiles(g, L, ntiles_total);
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        SegPair p = seg_pair(g, t, level);
+        const TilePair p = tile_pair(g, L, t);
         if (!p.active) continue;
-        const int64_t a_lo = split[t];
-        const int64_t a_hi = (p.x1 == p.pe) ? p.pm : split[t + 1];
-        const int64_t b_lo = p.pm + (p.x0 - p.ps) - (a_lo - p.ps);
-        const int64_t b_hi = p.pm + (p.x1 - p.ps) - (a_hi - p.ps);
-        cta_merge<K, V, THREADS, VT>(p.src ? buf_k1 : buf_k0, p.src ? buf_v1 : buf_v0, a_lo,
-                                     (int)(a_hi - a_lo), b_lo, (int)(b_hi - b_lo),
+        const Slice q = tile_slice(p, split, t);
+        cta_merge<K, V, THREADS, VT>(p.src ? buf_k1 : buf_k0, p.src ? buf_v1 : buf_v0, q.a_lo,
+                                     (int)(q.a_hi - q.a_lo), q.b_lo, (int)(q.b_hi - q.b_lo),
                                      p.dst ? buf_k1 : buf_k0, p.dst ? buf_v1 : buf_v0, p.x0, p.fin,
                                      codec, sk, sv);
         if (threadIdx.x == 0)
@@ -532,84 +579,273 @@ seg_merge_kernel(Geo g, int level, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, i
     }
 }
 
-// ---------------------------------------------------------------- cross-block rounds
+// ---------------------------------------------------------------- TMA pipeline helpers
 
-// Round r of the merge phase: groups of 2^r consecutive blocks are sorted
-// runs; pair k merges groups 2k and 2k+1 (the last group may be unpaired and
-// is copied).  Output tiles of T keys lie on a global grid, so one tile may
-// span several pairs.
-struct XPair {
-    int64_t ps, pm, pe;
-};
-__device__ __forceinline__ XPair x_pair(const Geo &g, int r, int64_t k) {
-    const int64_t G = int64_t(2) << r, H = int64_t(1) << r;
-    XPair p;
-    p.ps = clamp64(g.off[min(k * G, g.S)], 0, g.n);
-    p.pm = clamp64(g.off[min(k * G + H, g.S)], p.ps, g.n);
-    p.pe = clamp64(g.off[min(k * G + G, g.S)], p.pm, g.n);
-    return p;
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-
-struct XSplit {
-    int64_t k;  // pair holding the boundary (npairs for the end boundary)
-    int64_t a;  // absolute A index of the merge-path split
-};
-
-template <class K>
-__global__ void x_partition_kernel(Geo g, int r, const K *buf0, const K *buf1, XSplit *xs,
-                                   int64_t nbound) {
-    const K *src = ((g.R - r) & 1) ? buf1 : buf0;
-    const int64_t npairs = (g.S + (int64_t(2) << r) - 1) >> (r + 1);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nbound;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = min(t << g.logT, g.n);
-        XSplit out;
-        if (d >= g.n) {
-            out.k = npairs;
-            out.a = g.n;
-        } else {
-            const int64_t blk = seg_of(g, d);
-            out.k = blk >> (r + 1);
-            XPair p = x_pair(g, r, out.k);
-            auto A = [&](int64_t i) { return src[p.ps + i]; };
-            auto B = [&](int64_t i) { return src[p.pm + i]; };
-            out.a = p.ps + merge_path<K, int64_t>(A, p.pm - p.ps, B, p.pe - p.pm, d - p.ps);
-        }
-        xs[t] = out;
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on an mbarrier phase: gives up (false) once `limit_ns` of
+// global time has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
+// 1-D bulk copy global -> shared (TMA), completing `bytes` on the mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
 
-template <class K, class V, int THREADS, int VT>
-__global__ void __launch_bounds__(THREADS)
-xblock_merge_kernel(Geo g, int r, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
-                    const XSplit *__restrict__ xs, int64_t ntiles) {
+constexpr uint64_t WAIT_LIMIT = 2000000000ull;  // 2 s
+
+// Stage a[lo, hi) of a 16-byte aligned array of `n` items into shared memory
+// dst[0 ..): the 16-byte chunks by TMA, the ragged end past the array's last
+// full chunk by plain loads.  Returns the index in dst of item lo; adds the
+// TMA bytes to *tx.
+template <class T>
+__device__ __forceinline__ int stage_window(T *dst, const T *a, int64_t n, int64_t lo, int64_t hi,
+                                            uint64_t *bar, uint32_t *tx) {
+    constexpr int64_t E = 16 / sizeof(T);
+    const int64_t ws = lo & ~(E - 1);
+    if (hi <= lo) return (int)(lo - ws);
+    int64_t we = (hi + E - 1) & ~(E - 1);
+    const int64_t nfull = n & ~(E - 1);
+    if (we > nfull) we = nfull;  // never read past the array
+    if (we > ws) {
+        const uint32_t bytes = (uint32_t)((we - ws) * (int64_t)sizeof(T));
+        tma_load_1d(dst, a + ws, bytes, bar);
+        *tx += bytes;
+    } else {
+        we = ws;
+    }
+    for (int64_t x = we; x < hi; ++x) dst[x - ws] = a[x];  // at most E-1 items
+    return (int)(lo - ws);
+}
+
+// Descriptor of one staged tile, written by the producer next to its data.
+struct StageDesc {
+    int64_t o_lo;
+    int a_off, na, b_off, nb;  // key windows
+    int av_off, bv_off;        // value windows
+    int flags;                 // bit0 active, bit1 dst parity, bit2 final pass
+    int pad;
+};
+
+template <class K, class V, int TT> struct TmaLayout {
+    static constexpr int WIN = TT + 32 / (int)sizeof(K) + 2;  // items per key window
+    static constexpr int WINV = TT + 32 / (int)(sizeof(V) > 1 ? sizeof(V) : 4) + 2;
+    static constexpr size_t keys = ((size_t)WIN * sizeof(K) + 127) & ~size_t(127);
+    static constexpr size_t vals =
+        sizeof(V) > 1 ? (((size_t)WINV * sizeof(V) + 127) & ~size_t(127)) : 0;
+    static constexpr size_t stage = 2 * keys + 2 * vals + 128;  // A, B windows + descriptor
+};
+
+template <class K, class V, int THREADS, int VT, int STAGES>
+__host__ __device__ constexpr size_t tma_smem_bytes() {
+    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) + 128;
+}
+
+// Merge pass with a TMA pipeline (warp specialised, persistent).  The last
+// warp produces: for each of this CTA's tiles it computes the A and B slices
+// and stages them by 1-D bulk copies into a ring of STAGES shared-memory
+// stages (full/empty mbarriers).  THREADS consumer threads take each stage:
+// merge-path split, candidate merge of VT outputs per thread, 16-byte
+// vector stores straight to the output.  All waits are bounded; a timeout
+// records BS_ERR_TIMEOUT and ends the CTA.  Needs 16-byte aligned buffers.
+template <class K, class V, int THREADS, int VT, int STAGES>
+__global__ void __launch_bounds__(THREADS + 32)
+merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
+                 const int64_t *__restrict__ split, const int64_t *__restrict__ ntiles_total) {
     constexpr int TT = THREADS * VT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *sk = reinterpret_cast<K *>(smem_raw);
-    V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(TT));
-    const int src = (g.R - r) & 1, dst = (g.R - r - 1) & 1;
-    const bool fin = (r == g.R - 1);
-    const int64_t npairs = (g.S + (int64_t(2) << r) - 1) >> (r + 1);
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t d0 = t << g.logT, d1 = min(d0 + (int64_t(1) << g.logT), g.n);
-        const XSplit s0 = xs[t], s1 = xs[t + 1];
-        const int64_t klast = min(s1.k, npairs - 1);
-        for (int64_t kk = s0.k; kk <= klast; ++kk) {
-            XPair p = x_pair(g, r, kk);
-            const int64_t x_lo = max(p.ps, d0), x_hi = min(p.pe, d1);
-            if (x_hi <= x_lo) continue;
-            const int64_t a_lo = (kk == s0.k) ? s0.a : p.ps;
-            const int64_t a_hi = (kk == s1.k) ? s1.a : p.pm;
-            const int64_t b_lo = p.pm + (x_lo - p.ps) - (a_lo - p.ps);
-            const int64_t b_hi = p.pm + (x_hi - p.ps) - (a_hi - p.ps);
-            cta_merge<K, V, THREADS, VT>(src ? buf_k1 : buf_k0, src ? buf_v1 : buf_v0, a_lo,
-                                         (int)(a_hi - a_lo), b_lo, (int)(b_hi - b_lo),
-                                         dst ? buf_k1 : buf_k0, dst ? buf_v1 : buf_v0, x_lo, fin,
-                                         codec, sk, sv);
+    constexpr bool HV = HasVal<V>::value;
+    using LY = TmaLayout<K, V, TT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage);
+    uint64_t *empty = full + STAGES;
+    auto stage_a = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
+    auto stage_b = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage + LY::keys); };
+    auto stage_av = [&](int s) {
+        return reinterpret_cast<V *>(smem_raw + s * LY::stage + 2 * LY::keys);
+    };
+    auto stage_bv = [&](int s) {
+        return reinterpret_cast<V *>(smem_raw + s * LY::stage + 2 * LY::keys + LY::vals);
+    };
+    auto stage_desc = [&](int s) {
+        return reinterpret_cast<StageDesc *>(smem_raw + s * LY::stage + 2 * LY::keys + 2 * LY::vals);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], THREADS);
         }
-        if (threadIdx.x == 0)
-            atomicAdd(g.counters + CLS_MERGE,
-                      2ull * (sizeof(K) + (HasVal<V>::value ? sizeof(V) : 0)) * (d1 - d0));
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int64_t total = level_tiles(g, L, ntiles_total);
+    const int64_t n = g.n;
+
+    if (threadIdx.x >= THREADS) {
+        // ---------------- producer warp (one lane issues)
+        if (threadIdx.x != THREADS) return;
+        int64_t it = 0;
+        for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+            const int s = (int)(it % STAGES);
+            if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), WAIT_LIMIT)) {
+                if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
+                // drain: wait (bounded) for this CTA's copies still in flight
+                for (int64_t jt = (it > STAGES ? it - STAGES : 0); jt < it; ++jt)
+                    mbar_wait(&full[jt % STAGES], (uint32_t)((jt / STAGES) & 1), WAIT_LIMIT);
+                return;
+            }
+            const TilePair p = tile_pair(g, L, t);
+            StageDesc d{};
+            uint32_t issued = 0;
+            if (p.active) {
+                const Slice q = tile_slice(p, split, t);
+                const K *src = p.src ? buf_k1 : buf_k0;
+                d.o_lo = p.x0;
+                d.na = (int)(q.a_hi - q.a_lo);
+                d.nb = (int)(q.b_hi - q.b_lo);
+                d.flags = 1 | (p.dst << 1) | (p.fin ? 4 : 0);
+                // bulk copies first (they may complete before the expect below:
+                // the transaction count may go negative within a phase), then
+                // the plain writes, then the releasing arrive that publishes them
+                d.a_off = stage_window(stage_a(s), src, n, q.a_lo, q.a_hi, &full[s], &issued);
+                d.b_off = stage_window(stage_b(s), src, n, q.b_lo, q.b_hi, &full[s], &issued);
+                if constexpr (HV) {
+                    const V *srcv = p.src ? buf_v1 : buf_v0;
+                    d.av_off = stage_window(stage_av(s), srcv, n, q.a_lo, q.a_hi, &full[s], &issued);
+                    d.bv_off = stage_window(stage_bv(s), srcv, n, q.b_lo, q.b_hi, &full[s], &issued);
+                }
+            }
+            *stage_desc(s) = d;
+            mbar_arrive_expect_tx(&full[s], issued);
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int tid = threadIdx.x;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+        const int s = (int)(it % STAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), WAIT_LIMIT)) {
+            if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
+            return;
+        }
+        const StageDesc d = *stage_desc(s);
+        if (d.flags & 1) {
+            const K *sa = stage_a(s) + d.a_off;
+            const K *sb = stage_b(s) + d.b_off;
+            const int na = d.na, nb = d.nb, total_out = na + nb;
+            const int diag = min(tid * VT, total_out);
+            const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
+            const int j = diag - i;
+            const int count = min(VT, total_out - diag);
+            K k[VT];
+            uint32_t idx[VT];
+            // candidate merge straight from the staged windows (A before B)
+#pragma unroll
+            for (int u = 0; u < VT; ++u) {
+                const int ia = i + u, ib = j + VT - 1 - u;
+                if constexpr (HV) {
+                    K x = max_code<K>(), y = max_code<K>();
+                    uint32_t xi = 0xffffffffu, yi = 0xffffffffu;
+                    if (ia < na) x = sa[ia], xi = (uint32_t)ia;
+                    if (ib < nb) y = sb[ib], yi = (uint32_t)(na + ib);
+                    const bool tx = ki_less(x, xi, y, yi);
+                    k[u] = tx ? x : y;
+                    idx[u] = tx ? xi : yi;
+                } else {
+                    const K x = ia < na ? sa[ia] : max_code<K>();
+                    const K y = ib < nb ? sb[ib] : max_code<K>();
+                    k[u] = x < y ? x : y;
+                }
+            }
+            V v[VT];
+            if constexpr (HV) {
+                bitonic_merge_pairs<VT>(k, idx);
+                const V *sav = stage_av(s) + d.av_off;
+                const V *sbv = stage_bv(s) + d.bv_off;
+#pragma unroll
+                for (int u = 0; u < VT; ++u)
+                    if (u < count) v[u] = (int)idx[u] < na ? sav[idx[u]] : sbv[idx[u] - na];
+            } else {
+                bitonic_merge_keys<VT>(k);
+            }
+            // all shared reads of this stage are done: hand it back
+            mbar_arrive(&empty[s]);
+            const bool fin = (d.flags & 4) != 0;
+            K *dk = (d.flags & 2) ? buf_k1 : buf_k0;
+            const int64_t o = d.o_lo + diag;
+#pragma unroll
+            for (int u = 0; u < VT; ++u) k[u] = fin ? dec_code(k[u], codec) : k[u];
+            constexpr int E = 16 / sizeof(K);
+            if (count == VT && (o % E) == 0) {
+#pragma unroll
+                for (int u = 0; u < VT; u += E) {
+                    if constexpr (sizeof(K) == 4)
+                        *reinterpret_cast<uint4 *>(dk + o + u) =
+                            make_uint4((uint32_t)k[u], (uint32_t)k[u + 1], (uint32_t)k[u + 2], (uint32_t)k[u + 3]);
+                    else
+                        *reinterpret_cast<ulonglong2 *>(dk + o + u) =
+                            make_ulonglong2((unsigned long long)k[u], (unsigned long long)k[u + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < VT; ++u)
+                    if (u < count) dk[o + u] = k[u];
+            }
+            if constexpr (HV) {
+                V *dv = (d.flags & 2) ? buf_v1 : buf_v0;
+#pragma unroll
+                for (int u = 0; u < VT; ++u)
+                    if (u < count) dv[o + u] = v[u];
+            }
+            if (tid == 0)
+                atomicAdd(g.counters + CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
+        } else {
+            mbar_arrive(&empty[s]);
+        }
     }
 }
 

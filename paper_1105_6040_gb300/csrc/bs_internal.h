@@ -28,9 +28,37 @@ struct PassArgs {
     int Lmax;                 // in-segment merge levels to launch
     int64_t ntiles_ub;        // upper bound of the tile count (grid sizing)
     const int64_t *ntiles_total;  // device scalar: exact tile count
-    int64_t *split;           // per tile merge-path split (in-segment levels)
-    XSplit *xs;               // per global boundary split (cross-block rounds)
+    int64_t *split;           // per tile merge-path split of the current pass
+    int merge_impl;           // MERGE_SIMPLE or MERGE_TMA (the caller checked alignment)
 };
+
+enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };
+
+// Tiles of cross-block round r over S balanced blocks of n keys in total:
+// every pair gets *tpp tiles (enough for the longest pair, ceil(G*n/S) keys
+// with G = 2^(r+1) blocks per pair); returns npairs * tpp.
+inline int64_t xblock_tiles(int64_t n, int64_t S, int r, int logT, int64_t *tpp) {
+    const int64_t G = int64_t(2) << r;
+    const int64_t npairs = (S + G - 1) / G;
+    const unsigned __int128 gl = (unsigned __int128)(uint64_t)G * (uint64_t)n;
+    int64_t maxpair = (int64_t)((gl + (uint64_t)S - 1) / (uint64_t)S);
+    if (maxpair > n) maxpair = n;
+    const int64_t T = int64_t(1) << logT;
+    int64_t per = (maxpair + T - 1) / T;
+    if (per < 1) per = 1;
+    if (tpp) *tpp = per;
+    return npairs * per;
+}
+
+// Largest tile count of any cross-block round (0 when S <= 1).
+inline int64_t xblock_tiles_max(int64_t n, int64_t S, int logT) {
+    int64_t m = 0;
+    for (int r = 0; (int64_t(1) << r) < S; ++r) {
+        const int64_t x = xblock_tiles(n, S, r, logT, nullptr);
+        if (x > m) m = x;
+    }
+    return m;
+}
 
 bs_status run_passes_u32(const PassArgs &a, Launcher &L);
 bs_status run_passes_u64(const PassArgs &a, Launcher &L);

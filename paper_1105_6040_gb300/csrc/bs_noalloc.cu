@@ -148,8 +148,8 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     int64_t *tprefix = (int64_t *)take(sizeof(int64_t) * (p + 1));
     int64_t *bsum = (int64_t *)take(sizeof(int64_t) * 2);
     int32_t *tseg = (int32_t *)take(sizeof(int32_t) * ub);
-    int64_t *split = (int64_t *)take(sizeof(int64_t) * (ub + 1));
-    bs::XSplit *xs = (bs::XSplit *)take(sizeof(bs::XSplit) * (gtiles + 2));
+    const int64_t xt = bs::xblock_tiles_max(n, p, LOGT);
+    int64_t *split = (int64_t *)take(sizeof(int64_t) * ((ub > xt ? ub : xt) + 1));
     if (at > SCRATCH_BYTES) return BS_ERR_TOO_LARGE;  // cannot happen within the limits above
 
     if (cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 4, s) != cudaSuccess) {
@@ -194,7 +194,7 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     a.ntiles_ub = ub;
     a.ntiles_total = tprefix + p;
     a.split = split;
-    a.xs = xs;
+    a.merge_impl = (((uintptr_t)d_out | (uintptr_t)base) & 15) ? bs::MERGE_SIMPLE : bs::MERGE_AUTO;
     bs::Launcher L{s, nullptr, sms, no_begin, check_end};
     return kw == 4 ? bs::run_passes_u32(a, L) : bs::run_passes_u64(a, L);
 }

@@ -27,24 +27,37 @@ static inline int64_t grid_for(int64_t work, int64_t resident) {
     return g < 1 ? 1 : g;
 }
 
+// Shared memory a CTA may use while still leaving room for a second CTA.
+constexpr size_t TMA_SMEM_AUTO_LIMIT = 112 * 1024;
+constexpr size_t SMEM_OPT_IN_LIMIT = 227 * 1024;
+
 template <class K, class V, int THREADS, int KPT>
 bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     constexpr int T = THREADS * KPT;
+    constexpr int STAGES = 2;
     const size_t smem = smem_bytes<K, V>(T);
     const size_t tsmem = tile_smem_bytes<K, V>(T);
+    constexpr size_t msmem = tma_smem_bytes<K, V, THREADS, KPT, STAGES>();
     auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
-    auto sm = seg_merge_kernel<K, V, THREADS, KPT>;
-    auto xm = xblock_merge_kernel<K, V, THREADS, KPT>;
-    auto sp = seg_partition_kernel<K>;
-    auto xp = x_partition_kernel<K>;
-    // per-instantiation launch shape, computed once (idempotent, so a race
+    auto mk = merge_kernel<K, V, THREADS, KPT>;
+    auto mt = merge_tma_kernel<K, V, THREADS, KPT, STAGES>;
+    auto pk = partition_kernel<K>;
+    // per-instantiation launch shapes, computed once (idempotent, so a race
     // between host threads only repeats the same work)
-    static std::atomic<int> occ_ts{0}, occ_sm{0}, occ_xm{0};
+    static std::atomic<int> occ_ts{0}, occ_mk{0}, occ_mt{0};
     if (!occ_ts.load()) {
-        if (!allow_smem(ts, tsmem) || !allow_smem(sm, smem) || !allow_smem(xm, smem)) return BS_ERR_CUDA;
-        occ_sm.store(resident_ctas(sm, THREADS, smem));
-        occ_xm.store(resident_ctas(xm, THREADS, smem));
+        if (!allow_smem(ts, tsmem) || !allow_smem(mk, smem)) return BS_ERR_CUDA;
+        occ_mk.store(resident_ctas(mk, THREADS, smem));
+        if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem))
+            occ_mt.store(resident_ctas(mt, THREADS + 32, msmem));
+        else
+            occ_mt.store(-1);
         occ_ts.store(resident_ctas(ts, THREADS, tsmem));
+    }
+    bool tma = false;
+    if (occ_mt.load() > 0) {
+        if (a.merge_impl == MERGE_TMA) tma = true;
+        else if (a.merge_impl == MERGE_AUTO) tma = msmem <= TMA_SMEM_AUTO_LIMIT;
     }
     const Geo &g = a.g;
     K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
@@ -57,29 +70,32 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
     if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
 
+    // one merge pass: merge-path splits, then the merge kernel
+    auto pass = [&](const Level &lvl, int64_t tiles) -> bool {
+        L.begin(L.owner, CLS_PARTITION, L.stream);
+        pk<<<(unsigned)grid_for((tiles + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
+            g, lvl, k0, k1, a.split, a.ntiles_total);
+        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
+        L.begin(L.owner, CLS_MERGE, L.stream);
+        if (tma)
+            mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt), THREADS + 32, msmem, L.stream>>>(
+                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+        else
+            mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), THREADS, smem, L.stream>>>(
+                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+        return L.end(L.owner, CLS_MERGE, L.stream);
+    };
+
     // sort phase, continued: in-block merge levels
     for (int lv = 0; lv < a.Lmax; ++lv) {
-        L.begin(L.owner, CLS_PARTITION, L.stream);
-        sp<<<(unsigned)grid_for((a.ntiles_ub + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
-            g, lv, k0, k1, a.split, a.ntiles_total);
-        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return BS_ERR_CUDA;
-        L.begin(L.owner, CLS_MERGE, L.stream);
-        sm<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_sm), THREADS, smem, L.stream>>>(
-            g, lv, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-        if (!L.end(L.owner, CLS_MERGE, L.stream)) return BS_ERR_CUDA;
+        Level lvl{LEVEL_SEG, lv, 0, 0, 0};
+        if (!pass(lvl, a.ntiles_ub)) return BS_ERR_CUDA;
     }
-
-    // merge phase: cross-block rounds on a global grid of output tiles
-    const int64_t gtiles = (g.n + T - 1) / T;
+    // merge phase: cross-block rounds, tiles aligned to each pair's start
     for (int r = 0; r < g.R; ++r) {
-        L.begin(L.owner, CLS_PARTITION, L.stream);
-        xp<<<(unsigned)grid_for((gtiles + 1 + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
-            g, r, k0, k1, a.xs, gtiles + 1);
-        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return BS_ERR_CUDA;
-        L.begin(L.owner, CLS_MERGE, L.stream);
-        xm<<<(unsigned)grid_for(gtiles, (int64_t)L.sms * occ_xm), THREADS, smem, L.stream>>>(
-            g, r, k0, k1, v0, v1, a.codec, a.xs, gtiles);
-        if (!L.end(L.owner, CLS_MERGE, L.stream)) return BS_ERR_CUDA;
+        Level lvl{LEVEL_XBLOCK, 0, r, 0, 0};
+        lvl.ntiles = xblock_tiles(g.n, g.S, r, g.logT, &lvl.tpp);
+        if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
     }
     return BS_OK;
 }

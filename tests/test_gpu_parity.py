@@ -304,3 +304,50 @@ def test_2e28_int32_uniform_p2_sampled(sorter):
     for k in np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 13)]):
         lt, le = oracle.rank_bounds(cin, int(cout[k]))
         assert lt <= k < le, k
+
+
+# ------------------------------------------------------------------ merge kernels
+
+@pytest.mark.parametrize("merge_kernel", ["simple", "tma"])
+def test_merge_kernel_variants(merge_kernel):
+    """Both merge-pass kernels give the oracle's output on every key/value
+    type, ragged sizes, several p and segmented inputs."""
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0, merge_kernel=merge_kernel)
+    try:
+        for n, p in ((3 * T + 7, 1), (100003, 3), (1 << 18, 6), (262139, 64)):
+            check_keys(s, W.uniform_int32(n, n + p), p)
+            check_keys(s, W.uniform_uint64(n, n + p + 1), p)
+            check_keys(s, W.normal_float32_edges(n, n + p + 2), p)
+        for vmaker in (W.index_payload, lambda n: W.uniform_uint64(n, 9)):
+            for kmaker in (lambda n: W.uniform_int32(n, 8) % 300, lambda n: W.zipf_uint64(n, 7)):
+                n, p = 77777, 5
+                k, v = kmaker(n), vmaker(n)
+                ko, vo = s.sort_pairs(_to_dev(k), _to_dev(v), p=p)
+                s.sync()
+                wk, wv = oracle.sort(k, v, p=p)
+                assert np.array_equal(_bits(_to_host(ko)), _bits(wk))
+                assert np.array_equal(_bits(_to_host(vo)), _bits(wv))
+        lens = W.loguniform_lengths(400, 1, 1 << 15, seed=77)
+        off = W.offsets_from_lengths(lens)
+        k = W.uniform_int32(int(off[-1]), seed=78)
+        res = s.sort_segmented(_to_dev(k), torch.from_numpy(off).cuda())
+        s.sync()
+        assert np.array_equal(_to_host(res), oracle.sort_segmented(k, off)[0])
+    finally:
+        s.close()
+
+
+def test_unaligned_buffers_fall_back(sorter):
+    """Buffers that are not 16-byte aligned still sort correctly."""
+    x = W.uniform_int32(50001, 88)
+    base = torch.zeros(50001 + 3, dtype=torch.int32, device="cuda")
+    src = base[1:50002]
+    src.copy_(torch.from_numpy(x))
+    outb = torch.zeros(50001 + 3, dtype=torch.int32, device="cuda")
+    out = outb[3:50004]
+    from paper_1105_6040_gb300 import abi
+    abi.bs_sort_keys(sorter.h, src.data_ptr(), out.data_ptr(), x.size, "int32", 3,
+                     torch.cuda.current_stream().cuda_stream)
+    sorter.sync()
+    assert np.array_equal(out.cpu().numpy(), np.sort(x))
