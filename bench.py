@@ -45,6 +45,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["keys", "batched"], default="keys",
+                    help="keys: one 2^log2n int32 array (the headline); batched: many "
+                         "arrays of log-uniform length in one graph-captured segmented sort")
+    ap.add_argument("--segments", type=int, default=20000)
+    ap.add_argument("--seg-lo", type=int, default=16)
+    ap.add_argument("--seg-hi-log2", type=int, default=17)
+    ap.add_argument("--per-array-rounds", type=int, default=2)
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
@@ -75,9 +82,12 @@ def load_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_digest() -> str:
-    from paper_1105_6040_gb300 import build as b
-    return b._digest()
+def kernel_digest() -> str:
+    """Hash of the device code (all kernels live in csrc/bs_device.cuh): a
+    recorded ncu traffic figure is used only while this hash is unchanged."""
+    path = os.path.join(ROOT, "paper_1105_6040_gb300", "csrc", "bs_device.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def traffic_from_profiles(kernel: str, workload: str):
@@ -86,7 +96,7 @@ def traffic_from_profiles(kernel: str, workload: str):
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    digest = source_digest()
+    digest = kernel_digest()
     pat = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+sources=(\w+)")
     for name in sorted(os.listdir(pdir)):
         if not name.endswith((".md", ".txt")):
@@ -319,7 +329,7 @@ def run_ours(args):
                             "gbs": per_launch / (avg_ms * 1e-3) / 1e9 if per_launch else None}
     dom = max(("tile_sort", "merge"), key=lambda c: kms[c])
     achieved = kernels[dom]["gbs"]
-    traffic = traffic_from_profiles("seg_merge_kernel" if dom == "merge" else "tile_sort_kernel",
+    traffic = traffic_from_profiles("merge_tma_kernel" if dom == "merge" else "tile_sort_kernel",
                                     f"int32_2e{args.log2n}_p{args.p}_{args.dist}")
     passes = kernels["tile_sort"]["launches_per_step"] + kernels["merge"]["launches_per_step"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -377,10 +387,122 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched workload
+
+def run_batched(args):
+    """Many int32 arrays of log-uniform length sorted by one graph-captured
+    bs_sort_segmented, against one bs_sort_keys call per array."""
+    import numpy as np
+    import torch
+
+    from paper_1105_6040_gb300 import abi, autotune
+    from paper_1105_6040_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world != 1:
+        raise SystemExit("the batched workload runs on one GPU")
+    torch.cuda.set_device(local)
+    hi = 1 << args.seg_hi_log2
+    lens = W.loguniform_lengths(args.segments, args.seg_lo, hi, seed=SEED)
+    off = W.offsets_from_lengths(lens)
+    n = int(off[-1])
+    keys = W.uniform_int32(n, seed=SEED)
+    d_in = torch.from_numpy(keys).cuda()
+    d_out = torch.empty_like(d_in)
+    d_off = torch.from_numpy(off).cuda()
+    sorter = abi.Sorter(local)
+    t0 = time.perf_counter()
+    cfg = autotune.tune(sorter, "segmented", d_in, offsets=d_off, max_seg_len=hi, repeats=1)
+    tune_s = time.perf_counter() - t0
+    graph = sorter.capture_segmented(d_in, d_off, d_out, max_seg_len=hi)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        graph.launch(stream)
+    graph.sync()
+    # every segment nondecreasing (segment starts may drop)
+    starts = torch.zeros(n, dtype=torch.bool, device="cuda")
+    starts[d_off[:-1][lens > 0].clamp(max=n - 1)] = True
+    ok = (d_out[1:] >= d_out[:-1]) | starts[1:]
+    assert bool(ok.all()), "batched output not sorted per segment"
+
+    abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_batched = e0.elapsed_time(e1) / args.steps
+
+    # per-array baseline: one bs_sort_keys (p = 1) per array, same stream and buffers
+    sp = stream.cuda_stream
+    base_in, base_out = d_in.data_ptr(), d_out.data_ptr()
+
+    def per_array_round():
+        for i in range(args.segments):
+            if lens[i]:
+                abi.bs_sort_keys(sorter.h, base_in + 4 * int(off[i]), base_out + 4 * int(off[i]),
+                                 int(lens[i]), "int32", 1, sp)
+
+    abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    per_array_round()  # warm-up
+    torch.cuda.synchronize()
+    counts, _ = abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    per_array_launches = int(sum(counts.values()))
+    e0.record(stream)
+    for _ in range(args.per_array_rounds):
+        per_array_round()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_array = e0.elapsed_time(e1) / args.per_array_rounds
+    assert bool(((d_out[1:] >= d_out[:-1]) | starts[1:]).all())
+
+    # per-kernel timing of one uncaptured run
+    abi.bs_launch_stats(sorter.h, reset=True)
+    sorter.set_timing(True)
+    sorter.sort_segmented(d_in, d_off, kout=d_out, max_seg_len=hi)
+    sorter.sync()
+    sorter.set_timing(False)
+    kms, kn = sorter.kernel_times()
+    kcounts, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
+    peak, peak_src = load_peak()
+    kernels = {c: {"launches": kn[c], "ms": kms[c],
+                   "gbs": (kbytes[c] / (kms[c] * 1e-3) / 1e9) if kms[c] and kbytes[c] else None}
+               for c in kms if kn[c]}
+    graph.close()
+    sorter.close()
+    line = {
+        "metric": f"Gkeys/s, batched segmented int32 sort ({args.segments} arrays, "
+                  f"log-uniform lengths [{args.seg_lo}, 2^{args.seg_hi_log2}])",
+        "value": n / (ms_batched * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batched segmented sort, one CUDA-graph replay per step",
+                   "segments": args.segments, "total_keys": n, "seg_lo": args.seg_lo,
+                   "seg_hi": hi, "mean_len": n / args.segments, "autotuned": cfg,
+                   "autotune_s": tune_s, "seed": SEED},
+        "per_array": {"value": n / (ms_per_array * 1e-3) / 1e9, "unit": UNIT,
+                      "ms_per_step": ms_per_array, "launches_per_step": per_array_launches,
+                      "api": "one bs_sort_keys(p=1) per array, same stream"},
+        "speedup_vs_per_array": ms_per_array / ms_batched,
+        "kernels_one_run": kernels, "clocks": clk,
+        "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s",
+                     "peak_source": f"{peak_src} (copy bandwidth)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -177,6 +177,35 @@ bs_status bs_kernel_times(bs_handle *h, double *ms, int64_t *n);
  */
 bs_status bs_set_tile_log2(bs_handle *h, int tile_log2);
 
+/*
+ * CUDA graphs of whole sorts (the batching layer).  A captured graph replays
+ * every launch of one call with no host work per launch.  It owns a private
+ * handle whose workspace is sized before capture, so it stays valid however
+ * the creating handle is used later.  The graph refers to the buffers and the
+ * offsets array given at capture: refill them in place and replay.  A segmented
+ * graph is valid for any offsets with the same n, S and max_seg_len bound
+ * (segment descriptors are read from device memory at every replay).
+ * Capturing does not run the sort.
+ *
+ * bs_graph_capture_segmented: arguments as bs_sort_segmented; *g receives the
+ *   graph.  Errors: INVALID_ARG (n <= 0, S <= 0, NULL pointers),
+ *   UNSUPPORTED_DTYPE, OUT_OF_MEMORY, CUDA.
+ * bs_graph_capture_keys: arguments as bs_sort_keys (n > 0).
+ * bs_graph_launch: replay on `stream` (asynchronous).
+ * bs_graph_sync_status: as bs_sync_status, for the graph's launches.
+ * bs_graph_destroy: waits for the last replay, frees everything; NULL ok.
+ */
+typedef struct bs_graph bs_graph;
+bs_status bs_graph_capture_segmented(bs_handle *h, const void *d_kin, void *d_kout,
+                                     const void *d_vin, void *d_vout, int64_t n,
+                                     const int64_t *d_offsets, int64_t S, int64_t max_seg_len,
+                                     bs_dtype kt, bs_dtype vt, bs_graph **g);
+bs_status bs_graph_capture_keys(bs_handle *h, const void *d_in, void *d_out, int64_t n,
+                                bs_dtype kt, int64_t p, bs_graph **g);
+bs_status bs_graph_launch(bs_graph *g, void *stream);
+bs_status bs_graph_sync_status(bs_graph *g);
+bs_status bs_graph_destroy(bs_graph *g);
+
 /* Options of bs_set_option. */
 typedef enum {
     BS_OPT_TILE_LOG2 = 0,    /* value: 11, 12 or 13 (0 = default 12), as bs_set_tile_log2 */

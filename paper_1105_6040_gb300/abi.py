@@ -45,6 +45,12 @@ SIGNATURES = {
     "bs_set_tile_log2": ([_P, _INT], _INT),
     "bs_set_option": ([_P, _INT, _I64], _INT),
     "bs_sort_keys_noalloc": ([_P, _P, _I64, _INT, _I64, _P], _INT),
+    "bs_graph_capture_segmented": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT,
+                                    C.POINTER(C.c_void_p)], _INT),
+    "bs_graph_capture_keys": ([_P, _P, _P, _I64, _INT, _I64, C.POINTER(C.c_void_p)], _INT),
+    "bs_graph_launch": ([_P, _P], _INT),
+    "bs_graph_sync_status": ([_P], _INT),
+    "bs_graph_destroy": ([_P], _INT),
 }
 
 _lib = None
@@ -185,6 +191,62 @@ def bs_sort_keys_noalloc(d_in, d_out, n, kt, p, stream=0) -> None:
            "bs_sort_keys_noalloc")
 
 
+def bs_graph_capture_segmented(h, d_kin, d_kout, d_vin, d_vout, n, d_offsets, S, max_seg_len,
+                               kt, vt) -> int:
+    g = C.c_void_p()
+    _check(load().bs_graph_capture_segmented(h, d_kin, d_kout, d_vin, d_vout, int(n), d_offsets,
+                                             int(S), int(max_seg_len), dtype_code(kt),
+                                             dtype_code(vt), C.byref(g)),
+           "bs_graph_capture_segmented")
+    return g.value
+
+
+def bs_graph_capture_keys(h, d_in, d_out, n, kt, p) -> int:
+    g = C.c_void_p()
+    _check(load().bs_graph_capture_keys(h, d_in, d_out, int(n), dtype_code(kt), int(p),
+                                        C.byref(g)), "bs_graph_capture_keys")
+    return g.value
+
+
+def bs_graph_launch(g, stream=0) -> None:
+    _check(load().bs_graph_launch(g, stream or None), "bs_graph_launch")
+
+
+def bs_graph_sync_status(g) -> int:
+    return int(load().bs_graph_sync_status(g))
+
+
+def bs_graph_destroy(g) -> None:
+    _check(load().bs_graph_destroy(g), "bs_graph_destroy")
+
+
+class SortGraph:
+    """A captured sort (bs_graph_*): replay with launch(), free with close()."""
+
+    def __init__(self, g: int, keep=()):
+        self.g = g
+        self._keep = keep  # tensors the graph refers to
+
+    def launch(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        bs_graph_launch(self.g, int(s.cuda_stream))
+
+    def sync(self):
+        _check(bs_graph_sync_status(self.g), "bs_graph_sync_status")
+
+    def close(self):
+        if getattr(self, "g", None):
+            bs_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- torch front end
 
 
@@ -264,6 +326,24 @@ class Sorter:
                           keys.dtype, "none" if vals is None else vals.dtype,
                           _stream_ptr(stream, self.device))
         return (kout, vout) if vals is not None else kout
+
+    def capture_segmented(self, keys, offsets, kout, vals=None, vout=None, max_seg_len: int = 0):
+        """Capture bs_sort_segmented on these tensors into a replayable graph."""
+        for t, name in ((keys, "keys"), (offsets, "offsets"), (kout, "kout")):
+            self._check_tensor(t, name)
+        g = bs_graph_capture_segmented(
+            self.h, keys.data_ptr(), kout.data_ptr(),
+            None if vals is None else vals.data_ptr(), None if vals is None else vout.data_ptr(),
+            keys.numel(), offsets.data_ptr(), offsets.numel() - 1, max_seg_len, keys.dtype,
+            "none" if vals is None else vals.dtype)
+        return SortGraph(g, keep=(keys, offsets, kout, vals, vout))
+
+    def capture_keys(self, keys, out, p: int = 1):
+        self._check_tensor(keys, "keys")
+        self._check_tensor(out, "out")
+        g = bs_graph_capture_keys(self.h, keys.data_ptr(), out.data_ptr(), keys.numel(),
+                                  keys.dtype, p)
+        return SortGraph(g, keep=(keys, out))
 
     def sort_keys_host(self, h_in, h_out=None, p: int = 1):
         """Sort a host (CPU) tensor through the library's host-buffer entry point."""

@@ -641,4 +641,122 @@ bs_status bs_set_tile_log2(bs_handle *h, int tile_log2) {
     return BS_OK;
 }
 
+// ====================================================================== CUDA graphs
+
+}  // extern "C"
+
+struct bs_graph {
+    bs_handle *h = nullptr;  // private handle: owns the workspace the graph refers to
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+// Capture one call (run by `body` on the capture stream) into a graph that
+// owns a private handle with the workspace pre-sized to `ws_bytes`.
+template <class Body>
+bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out) {
+    *out = nullptr;
+    bs_graph *g = new (std::nothrow) bs_graph();
+    if (!g) return BS_ERR_OUT_OF_MEMORY;
+    bs_status st = bs_create(&g->h, h->device);
+    if (st != BS_OK) {
+        delete g;
+        return st;
+    }
+    g->h->logT = h->logT;
+    g->h->merge_impl = h->merge_impl;
+    DevGuard dg(h->device);
+    st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
+    if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)
+        st = BS_ERR_CUDA;
+    if (st == BS_OK) {
+        if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            st = BS_ERR_CUDA;
+        } else {
+            st = body(g->h, g->cap);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+            g->graph = graph;
+            if (st == BS_OK && (e != cudaSuccess || !graph)) st = BS_ERR_CUDA;
+            if (st == BS_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+                st = BS_ERR_CUDA;
+        }
+    }
+    if (st != BS_OK) {
+        cudaGetLastError();
+        bs_graph_destroy(g);
+        return st;
+    }
+    *out = g;
+    return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bs_status bs_graph_capture_segmented(bs_handle *h, const void *d_kin, void *d_kout,
+                                     const void *d_vin, void *d_vout, int64_t n,
+                                     const int64_t *d_offsets, int64_t S, int64_t max_seg_len,
+                                     bs_dtype kt, bs_dtype vt, bs_graph **out) {
+    if (!h || !out || n <= 0 || S <= 0 || max_seg_len < 0 || !d_offsets || !d_kin || !d_kout)
+        return BS_ERR_INVALID_ARG;
+    if (!key_width(kt) || (vt != BS_NONE && !value_width(vt))) return BS_ERR_UNSUPPORTED_DTYPE;
+    const size_t ws = ws_layout(n, S, (size_t)key_width(kt), (size_t)value_width(vt)).total;
+    return capture_graph(
+        h, ws,
+        [&](bs_handle *gh, cudaStream_t s) {
+            return bs_sort_segmented(gh, d_kin, d_kout, d_vin, d_vout, n, d_offsets, S, max_seg_len,
+                                     kt, vt, (void *)s);
+        },
+        out);
+}
+
+bs_status bs_graph_capture_keys(bs_handle *h, const void *d_in, void *d_out, int64_t n, bs_dtype kt,
+                                int64_t p, bs_graph **out) {
+    if (!h || !out || n <= 0 || p < 0 || !d_in || !d_out) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    const int64_t pp = p == 0 ? 1 : (p > n ? n : p);
+    const size_t ws = ws_layout(n, pp, (size_t)key_width(kt), 0).total;
+    return capture_graph(
+        h, ws,
+        [&](bs_handle *gh, cudaStream_t s) { return bs_sort_keys(gh, d_in, d_out, n, kt, p, (void *)s); },
+        out);
+}
+
+bs_status bs_graph_launch(bs_graph *g, void *stream) {
+    if (!g || !g->exec) return BS_ERR_INVALID_ARG;
+    DevGuard dg(g->h->device);
+    if (cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    g->last = (cudaStream_t)stream;
+    g->h->last_stream = (cudaStream_t)stream;
+    return BS_OK;
+}
+
+bs_status bs_graph_sync_status(bs_graph *g) {
+    if (!g) return BS_ERR_INVALID_ARG;
+    return bs_sync_status(g->h);
+}
+
+bs_status bs_graph_destroy(bs_graph *g) {
+    if (!g) return BS_OK;
+    if (g->h) {
+        DevGuard dg(g->h->device);
+        if (g->last) cudaStreamSynchronize(g->last);
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->cap) cudaStreamDestroy(g->cap);
+        bs_destroy(g->h);
+    }
+    delete g;
+    return BS_OK;
+}
+
 }  // extern "C"
