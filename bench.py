@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--seg-lo", type=int, default=16)
     ap.add_argument("--seg-hi-log2", type=int, default=17)
     ap.add_argument("--per-array-rounds", type=int, default=2)
+    ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16])
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
@@ -182,7 +183,7 @@ def workload_name(args) -> str:
 def config(args):
     return {"workload": workload_name(args), "n": 1 << args.log2n, "p": args.p,
             "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
-            "merge_kernel": args.merge,
+            "merge_kernel": args.merge, "merge_vt": args.merge_vt or 16,
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
             "stream": "torch current stream", "out_of_place": True}
 
@@ -270,7 +271,8 @@ def run_ours(args):
     # the CPU baseline copy (a prefix of the same workload) is taken before any big GPU work
     cpu_sample = keys_h[: 1 << min(args.cpu_sample_log2, args.log2n)].copy()
 
-    sorter = abi.Sorter(local, tile_log2=args.tile_log2, merge_kernel=args.merge)
+    sorter = abi.Sorter(local, tile_log2=args.tile_log2, merge_kernel=args.merge,
+                        merge_vt=args.merge_vt)
     d_in = torch.from_numpy(keys_h).cuda()
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()

@@ -209,7 +209,9 @@ bs_status bs_graph_destroy(bs_graph *g);
 /* Options of bs_set_option. */
 typedef enum {
     BS_OPT_TILE_LOG2 = 0,    /* value: 11, 12 or 13 (0 = default 12), as bs_set_tile_log2 */
-    BS_OPT_MERGE_KERNEL = 1  /* value: a bs_merge_kernel */
+    BS_OPT_MERGE_KERNEL = 1, /* value: a bs_merge_kernel */
+    BS_OPT_MERGE_VT = 2      /* keys per consumer thread of the TMA merge: 16 (0 = default)
+                                or 8 (twice the threads per tile, tiles <= 4096 keys) */
 } bs_option;
 
 /* Merge-pass kernels.  AUTO uses the TMA pipeline when the tile's stages fit

@@ -170,7 +170,7 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
     _check(load().bs_set_tile_log2(h, int(tile_log2)), "bs_set_tile_log2")
 
 
-OPTIONS = {"tile_log2": 0, "merge_kernel": 1}
+OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2}
 MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}
 
 
@@ -259,7 +259,8 @@ def _stream_ptr(stream, device) -> int:
 class Sorter:
     """A library handle on one CUDA device, taking torch tensors."""
 
-    def __init__(self, device=None, tile_log2: int = 0, merge_kernel: str = "auto"):
+    def __init__(self, device=None, tile_log2: int = 0, merge_kernel: str = "auto",
+                 merge_vt: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Sorter needs a CUDA device; there is no CPU path")
@@ -270,6 +271,8 @@ class Sorter:
             bs_set_tile_log2(self.h, tile_log2)
         if merge_kernel != "auto":
             bs_set_option(self.h, "merge_kernel", merge_kernel)
+        if merge_vt:
+            bs_set_option(self.h, "merge_vt", merge_vt)
 
     def close(self):
         if getattr(self, "h", None):

@@ -2,8 +2,10 @@
 
 The tunable knobs are the tile size T = 2^tile_log2 keys (128, 256 or 512
 threads per CTA, 16 keys per thread; T is both the sort-phase tile and the
-merge-pass output tile) and the merge-pass kernel (the TMA pipeline or the
-plain shared-memory one).  Results never depend on them; speed does.
+merge-pass output tile), the merge-pass kernel (the TMA pipeline or the
+plain shared-memory one) and, for the TMA pipeline, the keys per consumer
+thread (16, or 8 with twice the consumer warps).  Results never depend on
+them; speed does.
 
 ``tune(...)`` times every candidate on the caller's own inputs with CUDA
 events (after a warm-up run), keeps the fastest, and remembers it in a JSON
@@ -24,7 +26,9 @@ from . import abi
 
 TILE_LOG2 = (11, 12, 13)
 MERGE_KERNELS = ("auto", "simple")
-CANDIDATES = [(t, m) for t in TILE_LOG2 for m in MERGE_KERNELS]
+# (tile_log2, merge_kernel, merge_vt); 8 keys per consumer needs tiles <= 4096
+CANDIDATES = [(t, "auto", 16) for t in TILE_LOG2] + [(t, "auto", 8) for t in (11, 12)] + \
+    [(t, "simple", 16) for t in TILE_LOG2]
 
 _lock = threading.Lock()
 
@@ -80,6 +84,7 @@ def lookup(key: str):
 def apply(sorter: abi.Sorter, cfg: dict) -> None:
     abi.bs_set_option(sorter.h, "tile_log2", cfg["tile_log2"])
     abi.bs_set_option(sorter.h, "merge_kernel", cfg["merge_kernel"])
+    abi.bs_set_option(sorter.h, "merge_vt", cfg.get("merge_vt", 16))
 
 
 def _time_call(fn, repeats: int) -> float:
@@ -120,13 +125,14 @@ def tune(sorter: abi.Sorter, kind: str, keys, vals=None, offsets=None, p: int = 
             sorter.sort_segmented(keys, offsets, vals, kout=kout, vout=vout, max_seg_len=max_seg_len)
 
     timings = {}
-    for tile, merge in CANDIDATES:
-        apply(sorter, {"tile_log2": tile, "merge_kernel": merge})
-        timings[f"{tile}/{merge}"] = _time_call(run, repeats)
+    for tile, merge, vt in CANDIDATES:
+        apply(sorter, {"tile_log2": tile, "merge_kernel": merge, "merge_vt": vt})
+        timings[f"{tile}/{merge}/{vt}"] = _time_call(run, repeats)
     sorter.sync()
     best = min(timings, key=timings.get)
-    tile, merge = best.split("/")
-    cfg = {"tile_log2": int(tile), "merge_kernel": merge, "ms": timings[best], "timings_ms": timings}
+    tile, merge, vt = best.split("/")
+    cfg = {"tile_log2": int(tile), "merge_kernel": merge, "merge_vt": int(vt),
+           "ms": timings[best], "timings_ms": timings}
     with _lock:
         cache = _load()
         cache[key] = cfg

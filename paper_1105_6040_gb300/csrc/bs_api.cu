@@ -151,6 +151,7 @@ struct bs_handle {
     int64_t launches[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
     int logT = 12;
     int merge_impl = MERGE_AUTO;
+    int merge_vt = 16;
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -379,6 +380,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.split = (int64_t *)(ws + W.split);
     const uintptr_t al = (uintptr_t)kout | (uintptr_t)a.k1 | (uintptr_t)vout | (uintptr_t)a.v1;
     a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
+    a.merge_vt = h->merge_vt;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -628,6 +630,11 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value < BS_MERGE_AUTO || value > BS_MERGE_TMA) return BS_ERR_INVALID_ARG;
         h->merge_impl = (int)value;
         return BS_OK;
+    case BS_OPT_MERGE_VT:
+        if (value == 0) value = 16;
+        if (value != 8 && value != 16) return BS_ERR_INVALID_ARG;
+        h->merge_vt = (int)value;
+        return BS_OK;
     default:
         return BS_ERR_INVALID_ARG;
     }
@@ -669,6 +676,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     }
     g->h->logT = h->logT;
     g->h->merge_impl = h->merge_impl;
+    g->h->merge_vt = h->merge_vt;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

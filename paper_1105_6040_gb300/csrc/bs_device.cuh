@@ -229,6 +229,45 @@ __device__ __forceinline__ void bitonic_merge_pairs(K (&k)[N], uint32_t (&x)[N])
             if ((i & s) == 0) cas_pairs(k[i], x[i], k[i + s], x[i + s]);
 }
 
+// ---------------------------------------------------------------- warp-level bitonic merge
+
+// One merge round inside a warp, keys only.  Each lane holds N sorted keys;
+// groups of 2^r lanes hold sorted lists of N << r keys, and this round
+// merges adjacent pairs of such groups into lists of N << (r+1) keys, by a
+// bitonic merger written with register shuffles: a "flip" stage compares
+// element e of the first list with element 2m-1-e of the pair (partner lane
+// l ^ (2^(r+1)-1), register N-1-u); then half-cleaners with lane strides
+// 2^(r-1) .. 1 (shuffles) and register strides N/2 .. 1 (in-thread) finish
+// it.  Every stage sends the lower key of a compared pair to the lower
+// position, so the merged list is ascending in (lane, register) order.
+template <int N, class K> __device__ __forceinline__ K shfl_xor_k(K v, int mask) {
+    if constexpr (sizeof(K) == 4) {
+        return (K)__shfl_xor_sync(0xffffffffu, (uint32_t)v, mask);
+    } else {
+        const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, mask);
+        const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), mask);
+        return (K)(((uint64_t)hi << 32) | lo);
+    }
+}
+
+template <int N, class K> __device__ __forceinline__ void warp_merge_round(K (&k)[N], int r, int lane) {
+    const bool upper = (lane >> r) & 1;
+    K t[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) t[u] = shfl_xor_k<N>(k[N - 1 - u], (2 << r) - 1);
+#pragma unroll
+    for (int u = 0; u < N; ++u) k[u] = upper ? (k[u] < t[u] ? t[u] : k[u]) : (k[u] < t[u] ? k[u] : t[u]);
+    for (int ls = (1 << r) >> 1; ls > 0; ls >>= 1) {
+        const bool up = lane & ls;
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const K p = shfl_xor_k<N>(k[u], ls);
+            k[u] = up ? (k[u] < p ? p : k[u]) : (k[u] < p ? k[u] : p);
+        }
+    }
+    bitonic_merge_keys<N>(k);
+}
+
 // ---------------------------------------------------------------- candidate merge
 
 // The VT smallest items of the merge of sorted lists A = S[a0, a0+na) and
@@ -340,8 +379,15 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
         if constexpr (HV) reg_sort_pairs<KPT>(k, x);
         else reg_sort_keys<KPT>(k);
 
+        int r0 = 0;
+        if constexpr (!HV) {
+            // merges inside a warp: register shuffles, no shared memory
+            const int lane = tid & 31;
 #pragma unroll 1
-        for (int r = 0; (KPT << r) < T; ++r) {
+            for (; (2 << r0) <= 32 && (KPT << r0) < T; ++r0) warp_merge_round<KPT>(k, r0, lane);
+        }
+#pragma unroll 1
+        for (int r = r0; (KPT << r) < T; ++r) {
             const bool warp_round = (2 << r) <= 32;  // both lists inside one warp
 #pragma unroll
             for (int u = 0; u < KPT; ++u) {
@@ -679,7 +725,14 @@ template <class K, class V, int TT> struct TmaLayout {
 
 template <class K, class V, int THREADS, int VT, int STAGES>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) + 128;
+    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) +
+           STAGES * (THREADS + 1) * sizeof(int) + 128;
+}
+
+// Barrier among the consumer warps only (named barrier 1; the producer warp
+// never joins it).
+template <int N> __device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
 
 // Merge pass with a TMA pipeline (warp specialised, persistent).  The last
@@ -699,6 +752,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage);
     uint64_t *empty = full + STAGES;
+    int *ssplit = reinterpret_cast<int *>(empty + STAGES);  // STAGES x (THREADS + 1)
     auto stage_a = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
     auto stage_b = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage + LY::keys); };
     auto stage_av = [&](int s) {
@@ -779,25 +833,32 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             const int na = d.na, nb = d.nb, total_out = na + nb;
             const int diag = min(tid * VT, total_out);
             const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
-            const int j = diag - i;
+            // the next thread's split ends this thread's slice: exactly
+            // na_t items of A and nb_t of B (their merge is the output)
+            int *sp = ssplit + s * (THREADS + 1);
+            sp[tid] = i;
+            consumer_sync<THREADS>();
             const int count = min(VT, total_out - diag);
+            const int i_next = (diag + VT >= total_out) ? na : sp[tid + 1];
+            const int j = diag - i;
+            const int na_t = i_next - i, nb_t = count - na_t;
             K k[VT];
             uint32_t idx[VT];
-            // candidate merge straight from the staged windows (A before B)
+            // candidate merge on the exact slice: A' ++ reverse(B') is bitonic
 #pragma unroll
             for (int u = 0; u < VT; ++u) {
-                const int ia = i + u, ib = j + VT - 1 - u;
+                const int ub = VT - 1 - u;
                 if constexpr (HV) {
                     K x = max_code<K>(), y = max_code<K>();
                     uint32_t xi = 0xffffffffu, yi = 0xffffffffu;
-                    if (ia < na) x = sa[ia], xi = (uint32_t)ia;
-                    if (ib < nb) y = sb[ib], yi = (uint32_t)(na + ib);
+                    if (u < na_t) x = sa[i + u], xi = (uint32_t)(i + u);
+                    if (ub < nb_t) y = sb[j + ub], yi = (uint32_t)(na + j + ub);
                     const bool tx = ki_less(x, xi, y, yi);
                     k[u] = tx ? x : y;
                     idx[u] = tx ? xi : yi;
                 } else {
-                    const K x = ia < na ? sa[ia] : max_code<K>();
-                    const K y = ib < nb ? sb[ib] : max_code<K>();
+                    const K x = u < na_t ? sa[i + u] : max_code<K>();
+                    const K y = ub < nb_t ? sb[j + ub] : max_code<K>();
                     k[u] = x < y ? x : y;
                 }
             }
@@ -845,6 +906,9 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
                 atomicAdd(g.counters + CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
         } else {
             mbar_arrive(&empty[s]);
+            // keep one consumer barrier per tile, so a split buffer is never
+            // rewritten before every thread has read it two tiles earlier
+            consumer_sync<THREADS>();
         }
     }
 }

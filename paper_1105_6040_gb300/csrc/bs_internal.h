@@ -30,6 +30,7 @@ struct PassArgs {
     const int64_t *ntiles_total;  // device scalar: exact tile count
     int64_t *split;           // per tile merge-path split of the current pass
     int merge_impl;           // MERGE_SIMPLE or MERGE_TMA (the caller checked alignment)
+    int merge_vt;             // keys per consumer thread in the TMA merge: 16, or 8 (twice the warps)
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };

@@ -38,13 +38,18 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     const size_t smem = smem_bytes<K, V>(T);
     const size_t tsmem = tile_smem_bytes<K, V>(T);
     constexpr size_t msmem = tma_smem_bytes<K, V, THREADS, KPT, STAGES>();
+    // wide consumer shape: twice the threads, half the keys each, same tile
+    constexpr bool HAS_WIDE = 2 * THREADS + 32 <= 1024;
+    constexpr int WT = HAS_WIDE ? 2 * THREADS : THREADS, WVT = HAS_WIDE ? KPT / 2 : KPT;
+    constexpr size_t wsmem = tma_smem_bytes<K, V, WT, WVT, STAGES>();
     auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
     auto mk = merge_kernel<K, V, THREADS, KPT>;
     auto mt = merge_tma_kernel<K, V, THREADS, KPT, STAGES>;
+    auto mw = merge_tma_kernel<K, V, WT, WVT, STAGES>;
     auto pk = partition_kernel<K>;
     // per-instantiation launch shapes, computed once (idempotent, so a race
     // between host threads only repeats the same work)
-    static std::atomic<int> occ_ts{0}, occ_mk{0}, occ_mt{0};
+    static std::atomic<int> occ_ts{0}, occ_mk{0}, occ_mt{0}, occ_mw{0};
     if (!occ_ts.load()) {
         if (!allow_smem(ts, tsmem) || !allow_smem(mk, smem)) return BS_ERR_CUDA;
         occ_mk.store(resident_ctas(mk, THREADS, smem));
@@ -52,6 +57,10 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
             occ_mt.store(resident_ctas(mt, THREADS + 32, msmem));
         else
             occ_mt.store(-1);
+        if (HAS_WIDE && wsmem <= SMEM_OPT_IN_LIMIT && allow_smem(mw, wsmem))
+            occ_mw.store(resident_ctas(mw, WT + 32, wsmem));
+        else
+            occ_mw.store(-1);
         occ_ts.store(resident_ctas(ts, THREADS, tsmem));
     }
     bool tma = false;
@@ -59,6 +68,7 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         if (a.merge_impl == MERGE_TMA) tma = true;
         else if (a.merge_impl == MERGE_AUTO) tma = msmem <= TMA_SMEM_AUTO_LIMIT;
     }
+    const bool wide = tma && a.merge_vt == 8 && occ_mw.load() > 0;
     const Geo &g = a.g;
     K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
     V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
@@ -77,7 +87,10 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
             g, lvl, k0, k1, a.split, a.ntiles_total);
         if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
         L.begin(L.owner, CLS_MERGE, L.stream);
-        if (tma)
+        if (wide)
+            mw<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mw), WT + 32, wsmem, L.stream>>>(
+                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+        else if (tma)
             mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt), THREADS + 32, msmem, L.stream>>>(
                 g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
         else

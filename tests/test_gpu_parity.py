@@ -308,12 +308,12 @@ def test_2e28_int32_uniform_p2_sampled(sorter):
 
 # ------------------------------------------------------------------ merge kernels
 
-@pytest.mark.parametrize("merge_kernel", ["simple", "tma"])
-def test_merge_kernel_variants(merge_kernel):
-    """Both merge-pass kernels give the oracle's output on every key/value
+@pytest.mark.parametrize("merge_kernel,merge_vt", [("simple", 0), ("tma", 16), ("tma", 8)])
+def test_merge_kernel_variants(merge_kernel, merge_vt):
+    """Every merge-pass kernel gives the oracle's output on every key/value
     type, ragged sizes, several p and segmented inputs."""
     from paper_1105_6040_gb300.abi import Sorter
-    s = Sorter(0, merge_kernel=merge_kernel)
+    s = Sorter(0, merge_kernel=merge_kernel, merge_vt=merge_vt)
     try:
         for n, p in ((3 * T + 7, 1), (100003, 3), (1 << 18, 6), (262139, 64)):
             check_keys(s, W.uniform_int32(n, n + p), p)
