@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["keys", "batched"], default="keys",
+    ap.add_argument("--workload", choices=["keys", "batched", "serving"], default="keys",
                     help="keys: one 2^log2n int32 array (the headline); batched: many "
                          "arrays of log-uniform length in one graph-captured segmented sort")
     ap.add_argument("--segments", type=int, default=20000)
@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--seg-hi-log2", type=int, default=17)
     ap.add_argument("--per-array-rounds", type=int, default=2)
     ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16])
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
+    ap.add_argument("--streams", type=int, default=4, help="serving: execution slots")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
@@ -499,12 +502,53 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving workload
+
+def run_serving(args):
+    """Poisson sort requests (lengths log-uniform [2^10, 2^26], int32 / float32
+    50/50) served with continuous batching; p50/p99 latency and Gkeys/s."""
+    import torch
+
+    from paper_1105_6040_gb300 import serving as S
+
+    rank, world, local = dist_env()
+    if world != 1:
+        raise SystemExit("the serving workload runs on one GPU")
+    cfg = S.ServingConfig(rate=args.rate, duration=args.duration, streams=args.streams,
+                          seed=SEED)
+    clocks = ClockSampler(local)
+    clocks.start()
+    summary, reqs, ex = S.serve(cfg, device=local)
+    clk = clocks.stop()
+    ex.close()
+    line = {
+        "metric": "serving: p50/p99 latency (ms) and aggregate Gkeys/s, Poisson sort requests",
+        "value": summary["gkeys_per_s"], "unit": UNIT, "n_gpus": 1, "steps": summary["requests"],
+        "warmup": 0, "ms_per_step": summary["mean_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "p50_ms": summary["p50_ms"], "p99_ms": summary["p99_ms"],
+        "config": {"workload": "serving loop with continuous batching",
+                   **{k: v for k, v in dataclasses_asdict(cfg).items() if k != "keep_results"}},
+        "serving": summary, "clocks": clk,
+        "offered_gkeys_per_s": sum(r.n for r in reqs) / cfg.duration / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def dataclasses_asdict(x):
+    import dataclasses
+    return dataclasses.asdict(x)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -127,6 +127,21 @@ bs_status bs_sort_segmented(bs_handle *h, const void *d_kin, void *d_kout, const
                             int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream);
 
 /*
+ * Gathered batch (the serving layer): like bs_sort_segmented, but segment s
+ * reads its len_s = d_offsets[s+1] - d_offsets[s] keys (and values) from
+ * d_kin[d_src_offsets[s] ...] of an input array of n_in items, so requests
+ * resident anywhere in one buffer are sorted in one call without a gather
+ * copy; output segment s is d_kout[d_offsets[s] ...].  d_src_offsets: S
+ * int64 on the device.  A source range outside [0, n_in) is reported by
+ * bs_sync_status as INVALID_ARG (nothing outside the arrays is read).  The
+ * output must not overlap the input ranges it is read from.
+ */
+bs_status bs_sort_segmented_gather(bs_handle *h, const void *d_kin, int64_t n_in,
+                                   const int64_t *d_src_offsets, void *d_kout, const void *d_vin,
+                                   void *d_vout, int64_t n, const int64_t *d_offsets, int64_t S,
+                                   int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream);
+
+/*
  * Host-memory convenience: sort n keys from host buffer h_in into host
  * buffer h_out (may be equal), copying through the handle's device buffers
  * on the handle's internal stream; returns after the result is in h_out.

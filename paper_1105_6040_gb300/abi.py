@@ -36,6 +36,8 @@ SIGNATURES = {
     "bs_sort_pairs": ([_P, _P, _P, _P, _P, _I64, _INT, _INT, _I64, _P], _INT),
     "bs_sort_segmented": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT, _P], _INT),
     "bs_sort_keys_host": ([_P, _P, _P, _I64, _INT, _I64], _INT),
+    "bs_sort_segmented_gather": ([_P, _P, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT,
+                                  _P], _INT),
     "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
     "bs_sync_status": ([_P], _INT),
     "bs_status_str": ([_INT], C.c_char_p),
@@ -127,6 +129,14 @@ def bs_sort_segmented(h, d_kin, d_kout, d_vin, d_vout, n, d_offsets, S, max_seg_
     _check(load().bs_sort_segmented(h, d_kin, d_kout, d_vin, d_vout, int(n), d_offsets, int(S),
                                     int(max_seg_len), dtype_code(kt), dtype_code(vt),
                                     stream or None), "bs_sort_segmented")
+
+
+def bs_sort_segmented_gather(h, d_kin, n_in, d_src_offsets, d_kout, d_vin, d_vout, n, d_offsets,
+                             S, max_seg_len, kt, vt, stream=0) -> None:
+    _check(load().bs_sort_segmented_gather(h, d_kin, int(n_in), d_src_offsets, d_kout, d_vin,
+                                           d_vout, int(n), d_offsets, int(S), int(max_seg_len),
+                                           dtype_code(kt), dtype_code(vt), stream or None),
+           "bs_sort_segmented_gather")
 
 
 def bs_sort_keys_host(h, h_in, h_out, n, kt, p) -> None:
@@ -329,6 +339,21 @@ class Sorter:
                           keys.dtype, "none" if vals is None else vals.dtype,
                           _stream_ptr(stream, self.device))
         return (kout, vout) if vals is not None else kout
+
+    def sort_gathered(self, pool, src_offsets, offsets, kout=None, max_seg_len: int = 0,
+                      stream=None):
+        """Sort S segments whose keys sit at src_offsets[s] of `pool` into
+        kout[offsets[s] : offsets[s+1]] in one call (keys only)."""
+        import torch
+        for t, name in ((pool, "pool"), (src_offsets, "src_offsets"), (offsets, "offsets")):
+            self._check_tensor(t, name)
+        n = int(offsets[-1].item()) if kout is None else kout.numel()
+        kout = torch.empty(n, dtype=pool.dtype, device=pool.device) if kout is None else kout
+        bs_sort_segmented_gather(self.h, pool.data_ptr(), pool.numel(), src_offsets.data_ptr(),
+                                 kout.data_ptr(), None, None, kout.numel(), offsets.data_ptr(),
+                                 offsets.numel() - 1, max_seg_len, pool.dtype, "none",
+                                 _stream_ptr(stream, self.device))
+        return kout
 
     def capture_segmented(self, keys, offsets, kout, vals=None, vout=None, max_seg_len: int = 0):
         """Capture bs_sort_segmented on these tensors into a replayable graph."""

@@ -49,6 +49,17 @@ __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n
     }
 }
 
+// Gathered segments: segment s reads len_s items from src_off[s] of an input
+// array of n_in items.
+__global__ void validate_gather_kernel(const int64_t *off, const int64_t *src_off, int64_t S,
+                                       int64_t n_in, int *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = off[i + 1] - off[i], so = src_off[i];
+        if (so < 0 || len < 0 || so > n_in - len) atomicCAS(err, 0, (int)BS_ERR_INVALID_ARG);
+    }
+}
+
 constexpr int SCAN_TH = 256, SCAN_IT = 16, SCAN_BLOCK = SCAN_TH * SCAN_IT;
 
 __device__ __forceinline__ int64_t tiles_of(const int64_t *off, int64_t s, int64_t n, int logT) {
@@ -300,7 +311,8 @@ inline unsigned blocks_for(int64_t work, int threads, int cap) {
 // user_off holds S+1 segment offsets (no cross-block rounds).
 bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, void *vout, int64_t n,
                   bs_dtype kt, int vbytes, bool balanced, int64_t p, const int64_t *user_off,
-                  int64_t S, int64_t max_len, cudaStream_t stream) {
+                  int64_t S, int64_t max_len, cudaStream_t stream, const int64_t *src_off = nullptr,
+                  int64_t n_in = 0) {
     const int kw = key_width(kt);
     const int64_t blocks = balanced ? p : S;
     if (blocks > INT32_MAX) return BS_ERR_INVALID_ARG;
@@ -334,6 +346,14 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
                                                                             h->d_err);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
         g.off = user_off;
+        if (src_off) {
+            launch_begin(h, CLS_SETUP, stream);
+            validate_gather_kernel<<<blocks_for(S, 256, cap), 256, 0, stream>>>(user_off, src_off, S,
+                                                                               n_in, h->d_err);
+            if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+            g.src_off = src_off;
+            g.n_in = n_in;
+        }
     }
 
     // tile map: exclusive scan of tiles per block, then tile -> block
@@ -494,6 +514,26 @@ bs_status bs_sort_segmented(bs_handle *h, const void *d_kin, void *d_kout, const
     return do_sort(h, d_kin, d_kout, has_v ? d_vin : nullptr, has_v ? d_vout : nullptr, n, kt,
                    has_v ? value_width(vt) : 0, false, 0, d_offsets, S, max_seg_len,
                    (cudaStream_t)stream);
+}
+
+bs_status bs_sort_segmented_gather(bs_handle *h, const void *d_kin, int64_t n_in,
+                                   const int64_t *d_src_offsets, void *d_kout, const void *d_vin,
+                                   void *d_vout, int64_t n, const int64_t *d_offsets, int64_t S,
+                                   int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream) {
+    if (!h || n < 0 || n_in < 0 || S < 0 || max_seg_len < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    const bool has_v = (vt != BS_NONE);
+    if (has_v && !value_width(vt)) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0 && S == 0) return BS_OK;
+    if (S == 0 || !d_offsets || !d_src_offsets) return BS_ERR_INVALID_ARG;
+    if (n > 0 && (!d_kin || !d_kout)) return BS_ERR_INVALID_ARG;
+    if (has_v && n > 0 && (!d_vin || !d_vout)) return BS_ERR_INVALID_ARG;
+    if (!has_v && (d_vin || d_vout)) return BS_ERR_INVALID_ARG;
+    if (n == 0) return bs_sort_segmented(h, d_kin, d_kout, d_vin, d_vout, 0, d_offsets, S, 0, kt, vt, stream);
+    DevGuard dg(h->device);
+    return do_sort(h, d_kin, d_kout, has_v ? d_vin : nullptr, has_v ? d_vout : nullptr, n, kt,
+                   has_v ? value_width(vt) : 0, false, 0, d_offsets, S, max_seg_len,
+                   (cudaStream_t)stream, d_src_offsets, n_in);
 }
 
 bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,

@@ -93,6 +93,8 @@ struct Geo {
     int R;                   // number of cross-block merge rounds
     unsigned long long *counters;  // algorithmic bytes per kernel class (stats)
     int *err;                      // device status flag (nullable): first error wins
+    const int64_t *src_off;        // gathered input: segment s reads in[src_off[s] ..] (nullable)
+    int64_t n_in;                  // length of the input array when src_off is set
 };
 
 // kernel classes of the statistics counters (same order as the C ABI's)
@@ -362,6 +364,15 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
         const bool fin = (L + g.R) == 0;
         K *dst_k = par ? buf_k1 : buf_k0;
         V *dst_v = par ? buf_v1 : buf_v0;
+        // where this tile's keys come from: in place, or (gathered segments)
+        // from the segment's own offset in the input array, kept inside it
+        int64_t ibase = base;
+        int lcnt = cnt;
+        if (g.src_off) {
+            const int64_t len = shi - slo;
+            if (len <= g.n_in) ibase = clamp64(g.src_off[s], 0, g.n_in - len) + (base - slo);
+            else lcnt = 0;  // malformed request (flagged by the offset check): load nothing
+        }
 
         // striped, coalesced load; padding slots get the largest code (and,
         // for pairs, positions past every real one)
@@ -370,10 +381,10 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
 #pragma unroll
         for (int u = 0; u < KPT; ++u) {
             const int pos = tid + u * THREADS;
-            k[u] = pos < cnt ? enc_code(in_k[base + pos], codec) : max_code<K>();
+            k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
             if constexpr (HV) {
                 x[u] = (uint32_t)pos;
-                if (pos < cnt) sv[spad<V>(pos)] = in_v[base + pos];
+                if (pos < lcnt) sv[spad<V>(pos)] = in_v[ibase + pos];
             }
         }
         if constexpr (HV) reg_sort_pairs<KPT>(k, x);
