@@ -142,6 +142,22 @@ bs_status bs_sort_segmented_gather(bs_handle *h, const void *d_kin, int64_t n_in
                                    int64_t max_seg_len, bs_dtype kt, bs_dtype vt, void *stream);
 
 /*
+ * Merge phase only (the gather-to-master form of Sec. 3.2.2): d_kin holds
+ * `runs` runs that are each already sorted (nondecreasing in the dtype's
+ * order); run r is [h_run_offsets[r], h_run_offsets[r+1]).  The runs are
+ * merged pairwise, round after round, into d_kout (stable: equal keys keep
+ * run order, then position).  h_run_offsets is a HOST array of runs+1 int64
+ * with h_run_offsets[0] = 0, h_run_offsets[runs] = n, nondecreasing (checked
+ * synchronously: INVALID_ARG); it is read during the call only.  Values
+ * optional as in bs_sort_segmented.  Runs that are not sorted give an
+ * undefined (but in-bounds) result.  Used by the multi-GPU exchange sort to
+ * merge the runs one GPU receives.
+ */
+bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin,
+                        void *d_vout, int64_t n, const int64_t *h_run_offsets, int64_t runs,
+                        bs_dtype kt, bs_dtype vt, void *stream);
+
+/*
  * Host-memory convenience: sort n keys from host buffer h_in into host
  * buffer h_out (may be equal), copying through the handle's device buffers
  * on the handle's internal stream; returns after the result is in h_out.
@@ -225,8 +241,15 @@ bs_status bs_graph_destroy(bs_graph *g);
 typedef enum {
     BS_OPT_TILE_LOG2 = 0,    /* value: 11, 12 or 13 (0 = default 12), as bs_set_tile_log2 */
     BS_OPT_MERGE_KERNEL = 1, /* value: a bs_merge_kernel */
-    BS_OPT_MERGE_VT = 2      /* keys per consumer thread of the TMA merge: 16 (0 = default)
+    BS_OPT_MERGE_VT = 2,     /* keys per consumer thread of the TMA merge: 16 (0 = default)
                                 or 8 (twice the threads per tile, tiles <= 4096 keys) */
+    BS_OPT_WAIT_LIMIT_MS = 3,/* limit of every device-side wait, ms (0 = default 2000):
+                                a wait that runs out records BS_ERR_TIMEOUT and the
+                                kernel returns, leaving the context usable */
+    BS_OPT_TEST_WITHHOLD = 4 /* test hook, for failure-detection tests only: while set,
+                                each TMA merge pass withholds one stage of its first CTA,
+                                so that CTA's bounded waits run out and the call ends
+                                with BS_ERR_TIMEOUT (and an incomplete output) */
 } bs_option;
 
 /* Merge-pass kernels.  AUTO uses the TMA pipeline when the tile's stages fit

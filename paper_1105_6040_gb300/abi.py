@@ -36,6 +36,7 @@ SIGNATURES = {
     "bs_sort_pairs": ([_P, _P, _P, _P, _P, _I64, _INT, _INT, _I64, _P], _INT),
     "bs_sort_segmented": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT, _P], _INT),
     "bs_sort_keys_host": ([_P, _P, _P, _I64, _INT, _I64], _INT),
+    "bs_merge_runs": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _INT, _INT, _P], _INT),
     "bs_sort_segmented_gather": ([_P, _P, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT,
                                   _P], _INT),
     "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
@@ -139,6 +140,15 @@ def bs_sort_segmented_gather(h, d_kin, n_in, d_src_offsets, d_kout, d_vin, d_vou
            "bs_sort_segmented_gather")
 
 
+def bs_merge_runs(h, d_kin, d_kout, d_vin, d_vout, n, h_run_offsets, runs, kt, vt="none",
+                  stream=0) -> None:
+    import numpy as np
+    off = np.ascontiguousarray(h_run_offsets, dtype=np.int64)
+    _check(load().bs_merge_runs(h, d_kin, d_kout, d_vin, d_vout, int(n), off.ctypes.data,
+                                int(runs), dtype_code(kt), dtype_code(vt), stream or None),
+           "bs_merge_runs")
+
+
 def bs_sort_keys_host(h, h_in, h_out, n, kt, p) -> None:
     _check(load().bs_sort_keys_host(h, h_in, h_out, int(n), dtype_code(kt), int(p)),
            "bs_sort_keys_host")
@@ -180,7 +190,8 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
     _check(load().bs_set_tile_log2(h, int(tile_log2)), "bs_set_tile_log2")
 
 
-OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2}
+OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2, "wait_limit_ms": 3,
+           "test_withhold": 4}
 MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}
 
 
@@ -372,6 +383,17 @@ class Sorter:
         g = bs_graph_capture_keys(self.h, keys.data_ptr(), out.data_ptr(), keys.numel(),
                                   keys.dtype, p)
         return SortGraph(g, keep=(keys, out))
+
+    def merge_runs(self, keys, run_offsets, out=None, stream=None):
+        """Merge sorted runs keys[run_offsets[r]:run_offsets[r+1]] into one
+        sorted tensor (run_offsets: host sequence of runs+1 ints)."""
+        import torch
+        self._check_tensor(keys, "keys")
+        out = torch.empty_like(keys) if out is None else out
+        bs_merge_runs(self.h, keys.data_ptr(), out.data_ptr(), None, None, keys.numel(),
+                      run_offsets, len(run_offsets) - 1, keys.dtype, "none",
+                      _stream_ptr(stream, self.device))
+        return out
 
     def sort_keys_host(self, h_in, h_out=None, p: int = 1):
         """Sort a host (CPU) tensor through the library's host-buffer entry point."""

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "bs_internal.h"
@@ -163,6 +164,8 @@ struct bs_handle {
     int logT = 12;
     int merge_impl = MERGE_AUTO;
     int merge_vt = 16;
+    uint64_t wait_ns = 0;  // 0: the kernels' default limit
+    int withhold = 0;      // test hook (BS_OPT_TEST_WITHHOLD)
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -226,7 +229,7 @@ struct WsLayout {
 
 constexpr int64_t MIN_TILE = 2048;
 
-WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs) {
+WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs, int64_t extra_tiles = 0) {
     WsLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -241,7 +244,8 @@ WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs) {
     L.off = take((size_t)(S + 1) * 8);
     L.tprefix = take((size_t)(S + 1) * 8);
     L.bsum = take((size_t)((S + 1) / SCAN_BLOCK + 2) * 8);
-    const int64_t xt = xblock_tiles_max(n, S, 11);
+    int64_t xt = xblock_tiles_max(n, S, 11);
+    if (extra_tiles > xt) xt = extra_tiles;
     L.tseg = take((size_t)ub * 4);
     L.split = take((size_t)((ub > xt ? ub : xt) + 1) * 8);
     L.total = o;
@@ -330,6 +334,8 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     g.tseg = (const int32_t *)(ws + W.tseg);
     g.counters = h->d_counters;
     g.err = h->d_err;
+    g.wait_ns = h->wait_ns;
+    g.withhold = h->withhold;
     g.R = balanced ? ceil_log2(p) : 0;
 
     Launcher L{stream, h, h->sms, launch_begin, launch_end};
@@ -536,6 +542,90 @@ bs_status bs_sort_segmented_gather(bs_handle *h, const void *d_kin, int64_t n_in
                    (cudaStream_t)stream, d_src_offsets, n_in);
 }
 
+bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const void *d_vin,
+                        void *d_vout, int64_t n, const int64_t *h_run_offsets, int64_t runs,
+                        bs_dtype kt, bs_dtype vt, void *stream) {
+    if (!h || n < 0 || runs < 1 || !h_run_offsets) return BS_ERR_INVALID_ARG;
+    const int kw = key_width(kt);
+    if (!kw) return BS_ERR_UNSUPPORTED_DTYPE;
+    const bool has_v = (vt != BS_NONE);
+    const int vw = has_v ? value_width(vt) : 0;
+    if (has_v && !vw) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (h_run_offsets[0] != 0 || h_run_offsets[runs] != n) return BS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < runs; ++i)
+        if (h_run_offsets[i + 1] < h_run_offsets[i]) return BS_ERR_INVALID_ARG;
+    if (runs > INT32_MAX) return BS_ERR_INVALID_ARG;
+    if (n == 0) return BS_OK;
+    if (!d_kin || !d_kout || (has_v && (!d_vin || !d_vout))) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (runs == 1) {
+        if (d_kin != d_kout &&
+            cudaMemcpyAsync(d_kout, d_kin, (size_t)n * kw, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return BS_ERR_CUDA;
+        if (has_v && d_vin != d_vout &&
+            cudaMemcpyAsync(d_vout, d_vin, (size_t)n * vw, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return BS_ERR_CUDA;
+        return BS_OK;
+    }
+    // tiles per pair of every round, from the real run lengths
+    const int R = ceil_log2(runs);
+    const int64_t T = int64_t(1) << h->logT;
+    std::vector<int64_t> tpp(R);
+    int64_t need = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t G = int64_t(2) << r;
+        int64_t longest = 0;
+        for (int64_t k = 0; k * G < runs; ++k) {
+            const int64_t a = h_run_offsets[k * G], b = h_run_offsets[std::min(k * G + G, runs)];
+            longest = std::max(longest, b - a);
+        }
+        tpp[r] = std::max<int64_t>(1, (longest + T - 1) / T);
+        need = std::max(need, ((runs + G - 1) / G) * tpp[r]);
+    }
+    const WsLayout W = ws_layout(n, runs, (size_t)kw, (size_t)vw, need);
+    bs_status st = ensure_ws(h, W.total);
+    if (st != BS_OK) return st;
+    char *ws = (char *)h->ws;
+    int64_t *off = (int64_t *)(ws + W.off);
+    if (cudaMemcpyAsync(off, h_run_offsets, sizeof(int64_t) * (runs + 1), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return BS_ERR_CUDA;
+    Geo g{};
+    g.off = off;
+    g.S = runs;
+    g.n = n;
+    g.logT = h->logT;
+    g.R = R;
+    g.ntiles_ub = 0;
+    g.counters = h->d_counters;
+    g.err = h->d_err;
+    g.wait_ns = h->wait_ns;
+    g.withhold = h->withhold;
+    Launcher L{s, h, h->sms, launch_begin, launch_end};
+    PassArgs a{};
+    a.g = g;
+    a.in_k = d_kin;
+    a.in_v = has_v ? d_vin : nullptr;
+    a.k0 = d_kout;
+    a.k1 = ws + W.tmp_k;
+    a.v0 = has_v ? d_vout : nullptr;
+    a.v1 = has_v ? (void *)(ws + W.tmp_v) : nullptr;
+    a.codec = key_codec(kt);
+    a.vbytes = vw;
+    a.Lmax = 0;
+    a.ntiles_ub = 0;
+    a.ntiles_total = nullptr;
+    a.split = (int64_t *)(ws + W.split);
+    const uintptr_t al = (uintptr_t)d_kout | (uintptr_t)a.k1 | (uintptr_t)a.v0 | (uintptr_t)a.v1;
+    a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
+    a.merge_vt = h->merge_vt;
+    a.merge_only = true;
+    a.tpp_host = tpp.data();
+    return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
+}
+
 bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
                             int64_t p) {
     if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
@@ -669,6 +759,13 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
     case BS_OPT_MERGE_KERNEL:
         if (value < BS_MERGE_AUTO || value > BS_MERGE_TMA) return BS_ERR_INVALID_ARG;
         h->merge_impl = (int)value;
+        return BS_OK;
+    case BS_OPT_WAIT_LIMIT_MS:
+        if (value < 0 || value > 60000) return BS_ERR_INVALID_ARG;
+        h->wait_ns = (uint64_t)value * 1000000ull;
+        return BS_OK;
+    case BS_OPT_TEST_WITHHOLD:
+        h->withhold = value != 0;
         return BS_OK;
     case BS_OPT_MERGE_VT:
         if (value == 0) value = 16;

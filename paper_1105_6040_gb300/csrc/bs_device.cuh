@@ -95,6 +95,8 @@ struct Geo {
     int *err;                      // device status flag (nullable): first error wins
     const int64_t *src_off;        // gathered input: segment s reads in[src_off[s] ..] (nullable)
     int64_t n_in;                  // length of the input array when src_off is set
+    uint64_t wait_ns;              // limit of every bounded wait (0: the default)
+    int withhold;                  // test hook: CTA 0's producer withholds its first stage
 };
 
 // kernel classes of the statistics counters (same order as the C ABI's)
@@ -636,6 +638,18 @@ merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int cod
     }
 }
 
+// Encode a whole array into codes (and copy its values): the first step of
+// merging caller-sorted runs, whose keys arrive in their dtype.
+template <class K, class V>
+__global__ void encode_copy_kernel(const K *__restrict__ in_k, const V *__restrict__ in_v, K *out_k,
+                                   V *out_v, int64_t n, int codec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        out_k[i] = enc_code(in_k[i], codec);
+        if constexpr (HasVal<V>::value) out_v[i] = in_v[i];
+    }
+}
+
 // ---------------------------------------------------------------- TMA pipeline helpers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -690,7 +704,7 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
         : "memory");
 }
 
-constexpr uint64_t WAIT_LIMIT = 2000000000ull;  // 2 s
+constexpr uint64_t WAIT_LIMIT_DEFAULT = 2000000000ull;  // 2 s
 
 // Stage a[lo, hi) of a 16-byte aligned array of `n` items into shared memory
 // dst[0 ..): the 16-byte chunks by TMA, the ragged end past the array's last
@@ -736,14 +750,7 @@ template <class K, class V, int TT> struct TmaLayout {
 
 template <class K, class V, int THREADS, int VT, int STAGES>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) +
-           STAGES * (THREADS + 1) * sizeof(int) + 128;
-}
-
-// Barrier among the consumer warps only (named barrier 1; the producer warp
-// never joins it).
-template <int N> __device__ __forceinline__ void consumer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) + 128;
 }
 
 // Merge pass with a TMA pipeline (warp specialised, persistent).  The last
@@ -763,7 +770,6 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage);
     uint64_t *empty = full + STAGES;
-    int *ssplit = reinterpret_cast<int *>(empty + STAGES);  // STAGES x (THREADS + 1)
     auto stage_a = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
     auto stage_b = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage + LY::keys); };
     auto stage_av = [&](int s) {
@@ -787,6 +793,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
 
     const int64_t total = level_tiles(g, L, ntiles_total);
     const int64_t n = g.n;
+    const uint64_t WAIT_LIMIT = g.wait_ns ? g.wait_ns : WAIT_LIMIT_DEFAULT;
 
     if (threadIdx.x >= THREADS) {
         // ---------------- producer warp (one lane issues)
@@ -801,6 +808,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
                     mbar_wait(&full[jt % STAGES], (uint32_t)((jt / STAGES) & 1), WAIT_LIMIT);
                 return;
             }
+            if (g.withhold && blockIdx.x == 0 && it == 0) continue;  // test hook: nothing arrives
             const TilePair p = tile_pair(g, L, t);
             StageDesc d{};
             uint32_t issued = 0;
@@ -844,32 +852,26 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             const int na = d.na, nb = d.nb, total_out = na + nb;
             const int diag = min(tid * VT, total_out);
             const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
-            // the next thread's split ends this thread's slice: exactly
-            // na_t items of A and nb_t of B (their merge is the output)
-            int *sp = ssplit + s * (THREADS + 1);
-            sp[tid] = i;
-            consumer_sync<THREADS>();
-            const int count = min(VT, total_out - diag);
-            const int i_next = (diag + VT >= total_out) ? na : sp[tid + 1];
             const int j = diag - i;
-            const int na_t = i_next - i, nb_t = count - na_t;
+            const int count = min(VT, total_out - diag);
             K k[VT];
             uint32_t idx[VT];
-            // candidate merge on the exact slice: A' ++ reverse(B') is bitonic
+            // candidate merge straight from the staged windows (A before B);
+            // no barrier among the consumers, so every wait stays bounded
 #pragma unroll
             for (int u = 0; u < VT; ++u) {
-                const int ub = VT - 1 - u;
+                const int ia = i + u, ib = j + VT - 1 - u;
                 if constexpr (HV) {
                     K x = max_code<K>(), y = max_code<K>();
                     uint32_t xi = 0xffffffffu, yi = 0xffffffffu;
-                    if (u < na_t) x = sa[i + u], xi = (uint32_t)(i + u);
-                    if (ub < nb_t) y = sb[j + ub], yi = (uint32_t)(na + j + ub);
+                    if (ia < na) x = sa[ia], xi = (uint32_t)ia;
+                    if (ib < nb) y = sb[ib], yi = (uint32_t)(na + ib);
                     const bool tx = ki_less(x, xi, y, yi);
                     k[u] = tx ? x : y;
                     idx[u] = tx ? xi : yi;
                 } else {
-                    const K x = u < na_t ? sa[i + u] : max_code<K>();
-                    const K y = ub < nb_t ? sb[j + ub] : max_code<K>();
+                    const K x = ia < na ? sa[ia] : max_code<K>();
+                    const K y = ib < nb ? sb[ib] : max_code<K>();
                     k[u] = x < y ? x : y;
                 }
             }
@@ -917,9 +919,6 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
                 atomicAdd(g.counters + CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
         } else {
             mbar_arrive(&empty[s]);
-            // keep one consumer barrier per tile, so a split buffer is never
-            // rewritten before every thread has read it two tiles earlier
-            consumer_sync<THREADS>();
         }
     }
 }

@@ -31,6 +31,8 @@ struct PassArgs {
     int64_t *split;           // per tile merge-path split of the current pass
     int merge_impl;           // MERGE_SIMPLE or MERGE_TMA (the caller checked alignment)
     int merge_vt;             // keys per consumer thread in the TMA merge: 16, or 8 (twice the warps)
+    bool merge_only;          // the blocks are caller-sorted runs: no sort phase
+    const int64_t *tpp_host;  // merge_only: tiles per pair of each round (host array)
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };

@@ -196,6 +196,8 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     a.split = split;
     a.merge_impl = (((uintptr_t)d_out | (uintptr_t)base) & 15) ? bs::MERGE_SIMPLE : bs::MERGE_AUTO;
     a.merge_vt = 16;
+    a.merge_only = false;
+    a.tpp_host = nullptr;
     bs::Launcher L{s, nullptr, sms, no_begin, check_end};
     return kw == 4 ? bs::run_passes_u32(a, L) : bs::run_passes_u64(a, L);
 }

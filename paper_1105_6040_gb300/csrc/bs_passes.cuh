@@ -74,11 +74,20 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
     const int PT = 256;  // partition threads per CTA
 
-    // sort phase: every tile of every block
-    L.begin(L.owner, CLS_TILE_SORT, L.stream);
-    ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem, L.stream>>>(
-        g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
-    if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+    if (a.merge_only) {
+        // runs arrive sorted: encode them into the buffer the rounds start from
+        L.begin(L.owner, CLS_SETUP, L.stream);
+        encode_copy_kernel<K, V><<<(unsigned)grid_for((g.n + 255) / 256, (int64_t)L.sms * 8), 256, 0,
+                                   L.stream>>>((const K *)a.in_k, (const V *)a.in_v,
+                                               (g.R & 1) ? k1 : k0, (g.R & 1) ? v1 : v0, g.n, a.codec);
+        if (!L.end(L.owner, CLS_SETUP, L.stream)) return BS_ERR_CUDA;
+    } else {
+        // sort phase: every tile of every block
+        L.begin(L.owner, CLS_TILE_SORT, L.stream);
+        ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem, L.stream>>>(
+            g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
+        if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+    }
 
     // one merge pass: merge-path splits, then the merge kernel
     auto pass = [&](const Level &lvl, int64_t tiles) -> bool {
@@ -107,7 +116,12 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     // merge phase: cross-block rounds, tiles aligned to each pair's start
     for (int r = 0; r < g.R; ++r) {
         Level lvl{LEVEL_XBLOCK, 0, r, 0, 0};
-        lvl.ntiles = xblock_tiles(g.n, g.S, r, g.logT, &lvl.tpp);
+        if (a.tpp_host) {
+            lvl.tpp = a.tpp_host[r];
+            lvl.ntiles = ((g.S + (int64_t(2) << r) - 1) >> (r + 1)) * lvl.tpp;
+        } else {
+            lvl.ntiles = xblock_tiles(g.n, g.S, r, g.logT, &lvl.tpp);
+        }
         if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
     }
     return BS_OK;

@@ -1,0 +1,72 @@
+"""Merge phase over caller-sorted runs (bs_merge_runs) and the exchange sort
+on one GPU (world size 1), against the oracle bit for bit."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1105_6040_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sorter():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("lens", [
+    [5000, 7001], [1, 0, 30000, 2, 0], [4096] * 7, list(range(0, 6400, 100)),
+    [100000, 3, 3, 3], [0, 0, 0, 17],
+], ids=["two", "skewed_empty", "seven_equal", "64_growing", "one_big", "mostly_empty"])
+@pytest.mark.parametrize("dtype", ["int32", "uint64", "float32"])
+def test_merge_runs_matches_oracle(sorter, lens, dtype):
+    lens = np.array(lens, dtype=np.int64)
+    off = W.offsets_from_lengths(lens)
+    n = int(off[-1])
+    x = {"int32": W.uniform_int32(n, 1) % 5000, "uint64": W.uniform_uint64(n, 2),
+         "float32": W.normal_float32_edges(n, 3)}[dtype]
+    runs = np.concatenate([oracle.sort(x[off[i]:off[i + 1]])[0] for i in range(lens.size)]) \
+        if n else x
+    if dtype == "uint64":
+        d = torch.from_numpy(runs.view(np.int64)).cuda().view(torch.uint64)
+    else:
+        d = torch.from_numpy(runs).cuda()
+    out = sorter.merge_runs(d, off.tolist())
+    sorter.sync()
+    got = out.view(torch.int64).cpu().numpy().view(np.uint64) if dtype == "uint64" else out.cpu().numpy()
+    bits = np.uint32 if got.dtype.itemsize == 4 else np.uint64
+    assert np.array_equal(got.view(bits), oracle.sort(x)[0].view(bits))
+
+
+def test_merge_runs_rejects_bad_offsets(sorter):
+    from paper_1105_6040_gb300 import abi
+    d = torch.zeros(10, dtype=torch.int32, device="cuda")
+    for bad in ([0, 5, 3, 10], [1, 10], [0, 9]):
+        with pytest.raises(abi.BsError) as e:
+            sorter.merge_runs(d, bad)
+        assert e.value.status == abi.BS_ERR_INVALID_ARG
+
+
+def test_exchange_sort_one_rank_on_gpu(sorter):
+    import datetime
+    import torch.distributed as dist
+    from paper_1105_6040_gb300 import distributed as D
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29561")
+    dist.init_process_group("gloo", rank=0, world_size=1, timeout=datetime.timedelta(seconds=60))
+    try:
+        x = W.uniform_int32(300001, seed=9)
+        part = D.exchange_sort(torch.from_numpy(x).cuda())
+        assert np.array_equal(part.cpu().numpy(), oracle.sort(x)[0])
+        val, ms, keys = D.replica_throughput(x.size, 2.0)
+        assert keys == x.size and ms == 2.0
+    finally:
+        dist.destroy_process_group()

@@ -351,3 +351,26 @@ def test_unaligned_buffers_fall_back(sorter):
                      torch.cuda.current_stream().cuda_stream)
     sorter.sync()
     assert np.array_equal(out.cpu().numpy(), np.sort(x))
+
+
+# ------------------------------------------------------------------ failure detection
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """A stage that nothing fills: the merge pass's bounded waits run out, the
+    call reports BS_ERR_TIMEOUT, and the same handle sorts correctly after."""
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0, merge_kernel="tma")
+    try:
+        x = W.uniform_int32(1 << 16, seed=123)
+        d = _to_dev(x)
+        abi.bs_set_option(s.h, "wait_limit_ms", 100)
+        abi.bs_set_option(s.h, "test_withhold", 1)
+        s.sort_keys(d, p=1)
+        assert abi.bs_sync_status(s.h) == abi.BS_ERR_TIMEOUT
+        abi.bs_set_option(s.h, "test_withhold", 0)
+        out = s.sort_keys(d, p=1)
+        s.sync()
+        assert np.array_equal(_to_host(out), np.sort(x))
+    finally:
+        s.close()
