@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["keys", "batched", "serving"], default="keys",
+    ap.add_argument("--workload", choices=["keys", "batched", "serving", "memory", "psweep"],
+                    default="keys",
                     help="keys: one 2^log2n int32 array (the headline); batched: many "
                          "arrays of log-uniform length in one graph-captured segmented sort")
     ap.add_argument("--segments", type=int, default=20000)
@@ -536,6 +537,89 @@ def run_serving(args):
     return 0
 
 
+# ---------------------------------------------------------------- p sweep (Table 1 analogue)
+
+def run_psweep(args):
+    """Time against the number of blocks p for both merge-phase schedules (the
+    pairwise tree and Fig. 1's odd-even compare-split), the GPU analogue of
+    the paper's Exp. 1 / Table 1; plus the tree up to p = 4096."""
+    import torch
+
+    from paper_1105_6040_gb300 import abi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    n = 1 << args.log2n
+    x = torch.from_numpy(make_keys(args, 0)).cuda()
+    out = torch.empty_like(x)
+    rows = []
+    stream = torch.cuda.current_stream()
+    for sched in ("tree", "oddeven"):
+        ps = [1 << i for i in range(13)] if sched == "tree" else [1, 2, 4, 8, 16, 32, 64]
+        s = abi.Sorter(local, tile_log2=args.tile_log2)
+        abi.bs_set_option(s.h, "merge_schedule", sched)
+        for p in ps:
+            for _ in range(2):
+                s.sort_keys(x, out=out, p=p)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(2, min(args.steps, 10))
+            e0.record(stream)
+            for _ in range(reps):
+                s.sort_keys(x, out=out, p=p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            counts, _ = s.stats(reset=True)
+            rows.append({"schedule": sched, "p": p, "ms": ms, "gkeys_per_s": n / (ms * 1e-3) / 1e9,
+                         "merge_passes_per_sort": counts["merge"] / (reps + 2)})
+        assert bool((out[1:] >= out[:-1]).all())
+        s.close()
+    line = {"metric": f"time vs p, 2^{args.log2n} {args.dist} int32 keys (Table 1 analogue)",
+            "value": min(r["ms"] for r in rows), "unit": "ms", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic", "rows": rows,
+            "config": config(args)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- memory experiment
+
+def run_memory(args):
+    """Device memory against n with two blocks (the paper's Exp. 2 / Table 2
+    analogue): the scratch the library asks for (bs_workspace_bytes) and the
+    device memory one sort actually took (cudaMemGetInfo before and after)."""
+    import torch
+
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rows = []
+    for n in [int(2.5e6 + 5e5 * i) for i in range(6)]:  # Table 2's sizes for merge / quick sort
+        ws = abi.bs_workspace_bytes(n, 2, "int32")
+        x = torch.from_numpy(W.uniform_int32(n, seed=SEED)).cuda()
+        out = torch.empty_like(x)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        s = abi.Sorter(local)
+        s.sort_keys(x, out=out, p=2)
+        s.sync()
+        free1, _ = torch.cuda.mem_get_info()
+        s.close()
+        rows.append({"n": n, "workspace_bytes": ws, "device_bytes_taken": free0 - free1,
+                     "in_out_bytes": 8 * n,
+                     "bytes_per_item_total": (ws + 8 * n) / n})
+    line = {"metric": "device memory vs n, int32 keys, p=2 (Table 2 analogue)", "value": rows[-1]["bytes_per_item_total"],
+            "unit": "bytes/item", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "rows": rows,
+            "paper_context": {"merge_sort_bytes_per_item": 83.9, "quick_sort_bytes_per_item": 13.7,
+                              "bubble_sort_bytes_per_item": 11.8, "note": "2011 Windows process memory"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def dataclasses_asdict(x):
     import dataclasses
     return dataclasses.asdict(x)
@@ -549,6 +633,10 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "memory":
+        return run_memory(args)
+    if args.workload == "psweep":
+        return run_psweep(args)
     return run_ours(args)
 
 

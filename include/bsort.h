@@ -246,11 +246,20 @@ typedef enum {
     BS_OPT_WAIT_LIMIT_MS = 3,/* limit of every device-side wait, ms (0 = default 2000):
                                 a wait that runs out records BS_ERR_TIMEOUT and the
                                 kernel returns, leaving the context usable */
-    BS_OPT_TEST_WITHHOLD = 4 /* test hook, for failure-detection tests only: while set,
+    BS_OPT_TEST_WITHHOLD = 4,/* test hook, for failure-detection tests only: while set,
                                 each TMA merge pass withholds one stage of its first CTA,
                                 so that CTA's bounded waits run out and the call ends
                                 with BS_ERR_TIMEOUT (and an incomplete output) */
+    BS_OPT_MERGE_SCHEDULE = 5/* value: a bs_schedule (bs_sort_keys only) */
 } bs_option;
+
+/* Merge-phase schedules of bs_sort_keys (same output, different passes):
+ * TREE (default): ceil(log2 p) rounds merging pairs of sorted runs.
+ * ODDEVEN: Fig. 1 read literally -- p compare-split rounds alternating
+ *   between block pairs (0,1),(2,3).. and (1,2),(3,4)..; every block gets
+ *   the capacity ceil(n/p) (the shorter ones padded with +infinity), which
+ *   p rounds need to sort unequal blocks.  p passes instead of log2 p. */
+typedef enum { BS_SCHEDULE_TREE = 0, BS_SCHEDULE_ODDEVEN = 1 } bs_schedule;
 
 /* Merge-pass kernels.  AUTO uses the TMA pipeline when the tile's stages fit
  * two CTAs per SM and every buffer is 16-byte aligned; TMA uses it whenever

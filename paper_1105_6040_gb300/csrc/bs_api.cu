@@ -166,6 +166,7 @@ struct bs_handle {
     int merge_vt = 16;
     uint64_t wait_ns = 0;  // 0: the kernels' default limit
     int withhold = 0;      // test hook (BS_OPT_TEST_WITHHOLD)
+    int schedule = BS_SCHEDULE_TREE;
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -316,12 +317,18 @@ inline unsigned blocks_for(int64_t work, int threads, int cap) {
 bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, void *vout, int64_t n,
                   bs_dtype kt, int vbytes, bool balanced, int64_t p, const int64_t *user_off,
                   int64_t S, int64_t max_len, cudaStream_t stream, const int64_t *src_off = nullptr,
-                  int64_t n_in = 0) {
+                  int64_t n_in = 0, bool oddeven = false) {
     const int kw = key_width(kt);
     const int64_t blocks = balanced ? p : S;
     if (blocks > INT32_MAX) return BS_ERR_INVALID_ARG;
+    // odd-even schedule: the sort runs on p padded blocks of cap keys each
+    const int64_t slot_cap = oddeven ? (n + p - 1) / p : 0;
+    const int64_t n_user = n;
+    const void *kout_user = kout;
+    if (oddeven) n = slot_cap * p;
     const WsLayout W = ws_layout(n, blocks, (size_t)kw, (size_t)vbytes);
-    bs_status st = ensure_ws(h, W.total);
+    const size_t pad_bytes = oddeven ? (((size_t)n * kw + 255) & ~size_t(255)) : 0;
+    bs_status st = ensure_ws(h, W.total + pad_bytes);
     if (st != BS_OK) return st;
     char *ws = (char *)h->ws;
     h->last_stream = stream;
@@ -339,6 +346,18 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     g.R = balanced ? ceil_log2(p) : 0;
 
     Launcher L{stream, h, h->sms, launch_begin, launch_end};
+    int codec = key_codec(kt);
+    if (oddeven) {
+        // scatter + encode into the padded buffer A; then sort A in place
+        void *A = ws + W.total;
+        st = kw == 4 ? oddeven_scatter_u32(kin, A, n_user, p, slot_cap, codec, L)
+                     : oddeven_scatter_u64(kin, A, n_user, p, slot_cap, codec, L);
+        if (st != BS_OK) return st;
+        kin = A;
+        kout = A;
+        codec = CODEC_IDENT;
+        g.R = 0;
+    }
     const int cap = h->sms * 8;
     if (balanced) {
         int64_t *off = (int64_t *)(ws + W.off);
@@ -393,7 +412,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.k1 = ws + W.tmp_k;
     a.v0 = vout;
     a.v1 = vbytes ? (void *)(ws + W.tmp_v) : nullptr;
-    a.codec = key_codec(kt);
+    a.codec = codec;
     a.vbytes = vbytes;
     if (balanced) {
         a.Lmax = levels_for((n + p - 1) / p, g.logT);
@@ -407,7 +426,13 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     const uintptr_t al = (uintptr_t)kout | (uintptr_t)a.k1 | (uintptr_t)vout | (uintptr_t)a.v1;
     a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
     a.merge_vt = h->merge_vt;
-    return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
+    a.oddeven_rounds = oddeven ? (int)p : 0;
+    st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
+    if (st != BS_OK || !oddeven) return st;
+    // after p rounds the keys are in buffer (p & 1): decode the first n
+    const void *res = (p & 1) ? a.k1 : a.k0;
+    return kw == 4 ? oddeven_compact_u32(res, (void *)kout_user, n_user, key_codec(kt), L)
+                   : oddeven_compact_u64(res, (void *)kout_user, n_user, key_codec(kt), L);
 }
 
 int value_width(bs_dtype vt) {
@@ -479,6 +504,9 @@ bs_status bs_sort_keys(bs_handle *h, const void *d_in, void *d_out, int64_t n, b
     if (p == 0) p = 1;
     if (p > n) p = n;
     DevGuard dg(h->device);
+    if (h->schedule == BS_SCHEDULE_ODDEVEN && p >= 2)
+        return do_sort(h, d_in, d_out, nullptr, nullptr, n, kt, 0, true, p, nullptr, p, 0,
+                       (cudaStream_t)stream, nullptr, 0, true);
     return do_sort(h, d_in, d_out, nullptr, nullptr, n, kt, 0, true, p, nullptr, p, 0,
                    (cudaStream_t)stream);
 }
@@ -623,6 +651,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.merge_vt = h->merge_vt;
     a.merge_only = true;
     a.tpp_host = tpp.data();
+    a.oddeven_rounds = 0;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -767,6 +796,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
     case BS_OPT_TEST_WITHHOLD:
         h->withhold = value != 0;
         return BS_OK;
+    case BS_OPT_MERGE_SCHEDULE:
+        if (value != BS_SCHEDULE_TREE && value != BS_SCHEDULE_ODDEVEN) return BS_ERR_INVALID_ARG;
+        h->schedule = (int)value;
+        return BS_OK;
     case BS_OPT_MERGE_VT:
         if (value == 0) value = 16;
         if (value != 8 && value != 16) return BS_ERR_INVALID_ARG;
@@ -814,6 +847,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->logT = h->logT;
     g->h->merge_impl = h->merge_impl;
     g->h->merge_vt = h->merge_vt;
+    g->h->schedule = h->schedule;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

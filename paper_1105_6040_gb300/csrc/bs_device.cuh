@@ -528,11 +528,11 @@ __device__ __forceinline__ void cta_merge(const K *__restrict__ src_k, const V *
 // keys from its start (tpp tiles per pair for cross-block rounds, enough for
 // the longest pair; tiles past a pair's end are inactive), so an output tile
 // always lies inside one pair.
-enum : int { LEVEL_SEG = 0, LEVEL_XBLOCK = 1 };
+enum : int { LEVEL_SEG = 0, LEVEL_XBLOCK = 1, LEVEL_ODDEVEN = 2 };
 struct Level {
     int kind;
     int lv;          // LEVEL_SEG: level
-    int r;           // LEVEL_XBLOCK: round
+    int r;           // LEVEL_XBLOCK / LEVEL_ODDEVEN: round
     int64_t tpp;     // LEVEL_XBLOCK: tiles per pair
     int64_t ntiles;  // LEVEL_XBLOCK: npairs * tpp (LEVEL_SEG reads the tile count)
 };
@@ -563,6 +563,24 @@ __device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int6
         p.src = (Ls - L.lv + g.R) & 1;
         p.dst = (Ls - L.lv - 1 + g.R) & 1;
         p.fin = (L.lv == Ls - 1) && g.R == 0;
+    } else if (L.kind == LEVEL_ODDEVEN) {
+        // compare-split round r: even rounds pair blocks (0,1),(2,3)..; odd
+        // rounds leave block 0 alone and pair (1,2),(3,4)..; a block without
+        // a partner is copied.  Merging a pair in place is the compare-split:
+        // the lower block keeps the first |block| keys, the upper the rest.
+        const int64_t k = t / L.tpp, j = t - k * L.tpp;
+        const int64_t first = (L.r & 1) ? (k == 0 ? 0 : 2 * k - 1) : 2 * k;
+        const int64_t nblk = ((L.r & 1) && k == 0) ? 1 : 2;
+        const int64_t last = min(first + nblk, g.S);
+        p.ps = clamp64(g.off[min(first, g.S)], 0, g.n);
+        p.pe = clamp64(g.off[last], p.ps, g.n);
+        p.pm = last - first >= 2 ? clamp64(g.off[first + 1], p.ps, p.pe) : p.pe;
+        p.x0 = p.ps + j * T;
+        p.x1 = min(p.x0 + T, p.pe);
+        p.active = p.x0 < p.pe;
+        p.src = L.r & 1;
+        p.dst = (L.r + 1) & 1;
+        p.fin = false;
     } else {
         const int64_t k = t / L.tpp, j = t - k * L.tpp;
         const int64_t G = int64_t(2) << L.r, H = int64_t(1) << L.r;
@@ -648,6 +666,30 @@ __global__ void encode_copy_kernel(const K *__restrict__ in_k, const V *__restri
         out_k[i] = enc_code(in_k[i], codec);
         if constexpr (HasVal<V>::value) out_v[i] = in_v[i];
     }
+}
+
+// Odd-even schedule: scatter the n keys of p balanced blocks (bounds
+// floor(i*n/p)) into p slots of `cap` keys each, encoded; the slots past a
+// block's keys hold the largest code (+infinity sentinels).
+template <class K>
+__global__ void pad_scatter_kernel(const K *__restrict__ in, K *out, int64_t n, int64_t p, int64_t cap,
+                                   int codec) {
+    const int64_t total = p * cap;
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < total;
+         y += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = y / cap, l = y - i * cap;
+        const int64_t b0 = (int64_t)(((unsigned __int128)(uint64_t)i * (uint64_t)n) / (uint64_t)p);
+        const int64_t b1 = (int64_t)(((unsigned __int128)(uint64_t)(i + 1) * (uint64_t)n) / (uint64_t)p);
+        out[y] = l < b1 - b0 ? enc_code(in[b0 + l], codec) : max_code<K>();
+    }
+}
+
+// Odd-even schedule, last step: the first n slots hold the sorted keys.
+template <class K>
+__global__ void decode_copy_kernel(const K *__restrict__ in, K *out, int64_t n, int codec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dec_code(in[i], codec);
 }
 
 // ---------------------------------------------------------------- TMA pipeline helpers

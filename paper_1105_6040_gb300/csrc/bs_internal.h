@@ -33,6 +33,8 @@ struct PassArgs {
     int merge_vt;             // keys per consumer thread in the TMA merge: 16, or 8 (twice the warps)
     bool merge_only;          // the blocks are caller-sorted runs: no sort phase
     const int64_t *tpp_host;  // merge_only: tiles per pair of each round (host array)
+    int oddeven_rounds;       // > 0: after the sort phase, that many compare-split rounds
+                              // instead of the cross-block tree (keys only, padded blocks)
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };
@@ -65,5 +67,12 @@ inline int64_t xblock_tiles_max(int64_t n, int64_t S, int logT) {
 
 bs_status run_passes_u32(const PassArgs &a, Launcher &L);
 bs_status run_passes_u64(const PassArgs &a, Launcher &L);
+// odd-even schedule helpers (keys only)
+bs_status oddeven_scatter_u32(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
+                              Launcher &L);
+bs_status oddeven_scatter_u64(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
+                              Launcher &L);
+bs_status oddeven_compact_u32(const void *in, void *out, int64_t n, int codec, Launcher &L);
+bs_status oddeven_compact_u64(const void *in, void *out, int64_t n, int codec, Launcher &L);
 
 }  // namespace bs

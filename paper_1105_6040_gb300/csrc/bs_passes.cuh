@@ -113,6 +113,18 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         Level lvl{LEVEL_SEG, lv, 0, 0, 0};
         if (!pass(lvl, a.ntiles_ub)) return BS_ERR_CUDA;
     }
+    // merge phase, odd-even form: compare-split rounds over equal blocks
+    if (a.oddeven_rounds > 0) {
+        const int64_t cap = g.n / g.S;
+        const int64_t tpp = (2 * cap + T - 1) / T;
+        for (int r = 0; r < a.oddeven_rounds; ++r) {
+            Level lvl{LEVEL_ODDEVEN, 0, r, tpp, 0};
+            const int64_t npairs = (r & 1) ? 1 + g.S / 2 : (g.S + 1) / 2;
+            lvl.ntiles = npairs * tpp;
+            if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
+        }
+        return BS_OK;
+    }
     // merge phase: cross-block rounds, tiles aligned to each pair's start
     for (int r = 0; r < g.R; ++r) {
         Level lvl{LEVEL_XBLOCK, 0, r, 0, 0};
@@ -125,6 +137,23 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
     }
     return BS_OK;
+}
+
+template <class K>
+bs_status oddeven_scatter_t(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
+                            Launcher &L) {
+    L.begin(L.owner, CLS_SETUP, L.stream);
+    pad_scatter_kernel<K><<<(unsigned)grid_for((p * cap + 255) / 256, (int64_t)L.sms * 8), 256, 0,
+                            L.stream>>>((const K *)in, (K *)out, n, p, cap, codec);
+    return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
+}
+
+template <class K>
+bs_status oddeven_compact_t(const void *in, void *out, int64_t n, int codec, Launcher &L) {
+    L.begin(L.owner, CLS_SETUP, L.stream);
+    decode_copy_kernel<K><<<(unsigned)grid_for((n + 255) / 256, (int64_t)L.sms * 8), 256, 0, L.stream>>>(
+        (const K *)in, (K *)out, n, codec);
+    return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
 }
 
 // Dispatch on the value width and the tile shape (T = 2^logT = THREADS*16).

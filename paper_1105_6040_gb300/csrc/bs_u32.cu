@@ -3,4 +3,11 @@
 
 namespace bs {
 bs_status run_passes_u32(const PassArgs &a, Launcher &L) { return run_passes_k<uint32_t>(a, L); }
+bs_status oddeven_scatter_u32(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
+                           Launcher &L) {
+    return oddeven_scatter_t<uint32_t>(in, out, n, p, cap, codec, L);
+}
+bs_status oddeven_compact_u32(const void *in, void *out, int64_t n, int codec, Launcher &L) {
+    return oddeven_compact_t<uint32_t>(in, out, n, codec, L);
+}
 }  // namespace bs

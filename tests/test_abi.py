@@ -1,6 +1,8 @@
 """The C-ABI library builds, loads and exports every entry point include/bsort.h
 declares; host-side argument checks answer without a GPU (CPU only)."""
 import ctypes as C
+
+import numpy as np
 import os
 import re
 
@@ -67,3 +69,16 @@ def test_create_without_gpu_fails_cleanly():
     st = abi.load().bs_create(C.byref(h), 0)
     assert st in (abi.BS_ERR_CUDA, abi.BS_ERR_INVALID_ARG)
     assert not h.value
+
+
+def test_workspace_is_one_scratch_copy_plus_small_index_arrays():
+    """Memory model (the paper's Exp. 2 analogue): the scratch is one copy of
+    keys (and values) plus index arrays that grow with n / tile and p."""
+    for kt, vt, e in (("int32", "none", 4), ("uint64", "int32", 12), ("float64", "uint64", 16)):
+        for n in (2_500_000, 5_000_000, 1 << 26):
+            ws = abi.bs_workspace_bytes(n, 2, kt, vt)
+            assert e * n <= ws <= e * n + n // 64 + (1 << 16), (kt, vt, n, ws)
+    # linear in n: equal steps of n add equal bytes (Table 2's sizes)
+    steps = [abi.bs_workspace_bytes(int(2.5e6 + 5e5 * i), 2, "int32") for i in range(6)]
+    diffs = np.diff(steps)
+    assert diffs.max() - diffs.min() <= 1024

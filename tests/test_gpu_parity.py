@@ -374,3 +374,27 @@ def test_bounded_wait_runs_out_and_reports_timeout():
         assert np.array_equal(_to_host(out), np.sort(x))
     finally:
         s.close()
+
+
+# ------------------------------------------------------------------ odd-even schedule (Fig. 1)
+
+@pytest.mark.parametrize("n,p", [(4, 3), (10, 4), (5000, 3), (T * 5 + 3, 7), (100003, 16),
+                                 (1 << 18, 64), (300, 300), (77, 2)])
+def test_oddeven_schedule_matches_oracle(n, p):
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    try:
+        abi.bs_set_option(s.h, "merge_schedule", "oddeven")
+        for x in (W.uniform_int32(n, n + p) % 1000, W.reverse_int32(n),
+                  W.normal_float32_edges(n, 5)):
+            got = gpu_keys(s, x, p)
+            want, _ = oracle.sort(x, p=p, form="oddeven")
+            assert np.array_equal(_bits(got), _bits(want)), (n, p)
+        s.stats(reset=True)
+        s.sort_keys(_to_dev(W.uniform_int32(n, 1)), p=p)
+        counts, _ = s.stats(reset=True)
+        lv = max(0, int(np.ceil(np.log2(max(1, -(-n // p) / T))))) if -(-n // p) > T else 0
+        assert counts["merge"] == p + lv  # in-block levels, then exactly p compare-split rounds
+    finally:
+        s.close()
