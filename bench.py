@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["keys", "batched", "serving", "memory", "psweep"],
+    ap.add_argument("--workload", choices=["keys", "batched", "serving", "memory", "psweep",
+                                           "localsort"],
                     default="keys",
                     help="keys: one 2^log2n int32 array (the headline); batched: many "
                          "arrays of log-uniform length in one graph-captured segmented sort")
@@ -583,6 +584,46 @@ def run_psweep(args):
     return 0
 
 
+# ---------------------------------------------------------------- local sorts (Figs. 2-4)
+
+def run_localsort(args):
+    """Sort-phase tile sorts after the paper's three local sorts (merge,
+    bubble, quick) on one input: tile-sort kernel time and whole-sort time."""
+    import torch
+
+    from paper_1105_6040_gb300 import abi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    n = 1 << args.log2n
+    x = torch.from_numpy(make_keys(args, 0)).cuda()
+    out = torch.empty_like(x)
+    rows = []
+    for ls in ("merge", "quick", "bubble"):
+        s = abi.Sorter(local, tile_log2=args.tile_log2)
+        abi.bs_set_option(s.h, "local_sort", ls)
+        s.sort_keys(x, out=out, p=args.p)
+        s.sync()
+        s.stats(reset=True)
+        s.set_timing(True)
+        reps = 3
+        for _ in range(reps):
+            s.sort_keys(x, out=out, p=args.p)
+        s.sync()
+        s.set_timing(False)
+        kms, kn = s.kernel_times()
+        total = sum(kms.values()) / reps
+        rows.append({"local_sort": ls, "tile_sort_ms": kms["tile_sort"] / max(1, kn["tile_sort"]),
+                     "sort_ms": total, "gkeys_per_s": n / (total * 1e-3) / 1e9})
+        assert bool((out[1:] >= out[:-1]).all())
+        s.close()
+    line = {"metric": f"sort-phase tile sorts (Figs. 2-4), 2^{args.log2n} {args.dist} int32, p={args.p}",
+            "value": rows[0]["sort_ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "rows": rows, "config": config(args)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- memory experiment
 
 def run_memory(args):
@@ -637,6 +678,8 @@ def main():
         return run_memory(args)
     if args.workload == "psweep":
         return run_psweep(args)
+    if args.workload == "localsort":
+        return run_localsort(args)
     return run_ours(args)
 
 

@@ -250,8 +250,17 @@ typedef enum {
                                 each TMA merge pass withholds one stage of its first CTA,
                                 so that CTA's bounded waits run out and the call ends
                                 with BS_ERR_TIMEOUT (and an incomplete output) */
-    BS_OPT_MERGE_SCHEDULE = 5/* value: a bs_schedule (bs_sort_keys only) */
+    BS_OPT_MERGE_SCHEDULE = 5,/* value: a bs_schedule (bs_sort_keys only) */
+    BS_OPT_LOCAL_SORT = 6    /* value: a bs_local_sort (keys-only sorts; pair sorts always
+                                use the stable MERGE tile sort) */
 } bs_option;
+
+/* Sort-phase tile sorts, after the paper's three local sorts:
+ * MERGE (default): register bitonic network + merge rounds (merge sort, Fig. 3);
+ * BUBBLE: odd-even transposition over the tile (adjacent exchange, Fig. 2), O(T^2);
+ * QUICK: CTA quick sort with Fig. 4's middle pivot and '< pivot' partition
+ *   (quadratic on heavy duplicates, like the original). */
+typedef enum { BS_LOCAL_MERGE = 0, BS_LOCAL_BUBBLE = 1, BS_LOCAL_QUICK = 2 } bs_local_sort;
 
 /* Merge-phase schedules of bs_sort_keys (same output, different passes):
  * TREE (default): ceil(log2 p) rounds merging pairs of sorted runs.

@@ -191,8 +191,9 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
 
 
 OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2, "wait_limit_ms": 3,
-           "test_withhold": 4, "merge_schedule": 5}
+           "test_withhold": 4, "merge_schedule": 5, "local_sort": 6}
 SCHEDULES = {"tree": 0, "oddeven": 1}
+LOCAL_SORTS = {"merge": 0, "bubble": 1, "quick": 2}
 MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}
 
 
@@ -200,7 +201,8 @@ def bs_set_option(h, option, value) -> None:
     if isinstance(option, str):
         option = OPTIONS[option]
     if isinstance(value, str):
-        value = SCHEDULES[value] if option == OPTIONS["merge_schedule"] else MERGE_KERNELS[value]
+        value = {OPTIONS["merge_schedule"]: SCHEDULES,
+                 OPTIONS["local_sort"]: LOCAL_SORTS}.get(option, MERGE_KERNELS)[value]
     _check(load().bs_set_option(h, int(option), int(value)), "bs_set_option")
 
 

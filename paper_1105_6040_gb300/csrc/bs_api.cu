@@ -167,6 +167,7 @@ struct bs_handle {
     uint64_t wait_ns = 0;  // 0: the kernels' default limit
     int withhold = 0;      // test hook (BS_OPT_TEST_WITHHOLD)
     int schedule = BS_SCHEDULE_TREE;
+    int local_sort = BS_LOCAL_MERGE;
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -427,6 +428,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
     a.merge_vt = h->merge_vt;
     a.oddeven_rounds = oddeven ? (int)p : 0;
+    a.local_sort = h->local_sort;
     st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
     if (st != BS_OK || !oddeven) return st;
     // after p rounds the keys are in buffer (p & 1): decode the first n
@@ -652,6 +654,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.merge_only = true;
     a.tpp_host = tpp.data();
     a.oddeven_rounds = 0;
+    a.local_sort = 0;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -796,6 +799,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
     case BS_OPT_TEST_WITHHOLD:
         h->withhold = value != 0;
         return BS_OK;
+    case BS_OPT_LOCAL_SORT:
+        if (value < BS_LOCAL_MERGE || value > BS_LOCAL_QUICK) return BS_ERR_INVALID_ARG;
+        h->local_sort = (int)value;
+        return BS_OK;
     case BS_OPT_MERGE_SCHEDULE:
         if (value != BS_SCHEDULE_TREE && value != BS_SCHEDULE_ODDEVEN) return BS_ERR_INVALID_ARG;
         h->schedule = (int)value;
@@ -848,6 +855,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->merge_impl = h->merge_impl;
     g->h->merge_vt = h->merge_vt;
     g->h->schedule = h->schedule;
+    g->h->local_sort = h->local_sort;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -449,6 +449,199 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
     }
 }
 
+// ---------------------------------------------------------------- tile sorts after Figs. 2 and 4
+
+// Tile bookkeeping shared by the alternative tile sorts (keys only).
+struct TileInfo {
+    int64_t base, ibase;
+    int cnt, lcnt;
+    bool fin;
+    int par;
+};
+__device__ __forceinline__ TileInfo tile_info(const Geo &g, int64_t t, int T) {
+    TileInfo ti;
+    const int64_t s = g.tseg[t];
+    int64_t slo, shi;
+    seg_bounds(g, s, slo, shi);
+    const int64_t j = t - g.tprefix[s];
+    ti.base = slo + j * T;
+    ti.cnt = (int)(shi - ti.base < (int64_t)T ? shi - ti.base : (int64_t)T);
+    const int L = seg_levels(shi - slo, g.logT);
+    ti.par = (L + g.R) & 1;
+    ti.fin = (L + g.R) == 0;
+    ti.ibase = ti.base;
+    ti.lcnt = ti.cnt;
+    if (g.src_off) {
+        const int64_t len = shi - slo;
+        if (len <= g.n_in) ti.ibase = clamp64(g.src_off[s], 0, g.n_in - len) + (ti.base - slo);
+        else ti.lcnt = 0;
+    }
+    return ti;
+}
+
+// Fig. 2 on a GPU: bubble sort's adjacent exchange, run as odd-even
+// transposition over the tile in shared memory -- cnt rounds, each
+// comparing the pairs (i, i+1) with i of the round's parity and exchanging
+// them on a strict '>'.  O(T^2) work per tile, like the paper's O(s^2).
+template <class K, int THREADS, int KPT>
+__global__ void __launch_bounds__(THREADS)
+tile_bubble_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int codec,
+                   const int64_t *__restrict__ ntiles_total) {
+    constexpr int T = THREADS * KPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    K *sk = reinterpret_cast<K *>(smem_raw);
+    const int64_t total = min(*ntiles_total, g.ntiles_ub);
+    const int tid = threadIdx.x;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const TileInfo ti = tile_info(g, t, T);
+        for (int pos = tid; pos < T; pos += THREADS)
+            sk[pos] = pos < ti.lcnt ? enc_code(in_k[ti.ibase + pos], codec) : max_code<K>();
+        __syncthreads();
+        for (int rd = 0; rd < ti.cnt; ++rd) {
+            for (int i = 2 * tid + (rd & 1); i + 1 < ti.cnt; i += 2 * THREADS) {
+                const K a = sk[i], b = sk[i + 1];
+                if (b < a) sk[i] = b, sk[i + 1] = a;
+            }
+            __syncthreads();
+        }
+        K *dst = ti.par ? buf_k1 : buf_k0;
+        for (int pos = tid; pos < ti.cnt; pos += THREADS) {
+            const K c = sk[pos];
+            dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
+        }
+        if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
+        __syncthreads();
+    }
+}
+
+// Block-wide exclusive scan of one int per thread; returns the total.
+template <int THREADS>
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int &excl) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int i = 0; i < THREADS / 32; ++i) {
+        const int ws = warp_sums[i];
+        if (i < w) before += ws;
+        total += ws;
+    }
+    excl = before + x - v;
+    __syncthreads();
+    return total;
+}
+
+// Fig. 4 on a GPU: quick sort of the tile in shared memory.  A segment
+// [lo, hi) longer than QS_SMALL is partitioned around its middle element
+// (the pivot choice of Fig. 4): keys '< pivot' first, then the pivot, then
+// the rest -- in parallel, by block scans of the per-thread counts -- and
+// its two sides are pushed on a stack; shorter segments are finished by one
+// thread each with insertion sort.  Keys equal to the pivot all go right, as
+// in Fig. 4, so heavy duplicates make it quadratic like the original.
+constexpr int QS_SMALL = 32;
+
+template <class K, int THREADS, int KPT>
+__global__ void __launch_bounds__(THREADS)
+tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int codec,
+                  const int64_t *__restrict__ ntiles_total) {
+    constexpr int T = THREADS * KPT;
+    constexpr int MAXSTACK = T / QS_SMALL + 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    K *sk = reinterpret_cast<K *>(smem_raw);
+    K *tmp = sk + T;
+    int2 *stack = reinterpret_cast<int2 *>(tmp + T);
+    int2 *small = stack + MAXSTACK;                  // up to T short segments
+    int *warp_sums = reinterpret_cast<int *>(small + T);
+    __shared__ int top, nsmall, seg_lo, seg_hi;
+    const int64_t total = min(*ntiles_total, g.ntiles_ub);
+    const int tid = threadIdx.x;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const TileInfo ti = tile_info(g, t, T);
+        for (int pos = tid; pos < T; pos += THREADS)
+            sk[pos] = pos < ti.lcnt ? enc_code(in_k[ti.ibase + pos], codec) : max_code<K>();
+        if (tid == 0) {
+            top = 0;
+            nsmall = 0;
+            if (ti.cnt > QS_SMALL) stack[top++] = make_int2(0, ti.cnt);
+            else if (ti.cnt > 1) small[nsmall++] = make_int2(0, ti.cnt);
+        }
+        __syncthreads();
+        while (top > 0) {
+            if (tid == 0) {
+                const int2 sg = stack[--top];
+                seg_lo = sg.x;
+                seg_hi = sg.y;
+            }
+            __syncthreads();
+            const int lo = seg_lo, hi = seg_hi, len = hi - lo, mid = lo + len / 2;
+            const K pivot = sk[mid];
+            // this thread's chunk of the segment
+            const int per = (len + THREADS - 1) / THREADS;
+            const int c0 = min(lo + tid * per, hi), c1 = min(c0 + per, hi);
+            int nl = 0, nr = 0;
+            for (int x = c0; x < c1; ++x) {
+                if (x == mid) continue;
+                if (sk[x] < pivot) ++nl;
+                else ++nr;
+            }
+            int el, er;
+            const int tl = block_excl_scan<THREADS>(nl, warp_sums, el);
+            block_excl_scan<THREADS>(nr, warp_sums, er);
+            int wl = lo + el, wr = lo + tl + 1 + er;
+            for (int x = c0; x < c1; ++x) {
+                if (x == mid) continue;
+                const K v = sk[x];
+                if (v < pivot) tmp[wl++] = v;
+                else tmp[wr++] = v;
+            }
+            if (tid == 0) tmp[lo + tl] = pivot;
+            __syncthreads();
+            for (int x = lo + tid; x < hi; x += THREADS) sk[x] = tmp[x];
+            if (tid == 0) {
+                const int2 sides[2] = {make_int2(lo, lo + tl), make_int2(lo + tl + 1, hi)};
+                for (int q = 0; q < 2; ++q) {
+                    const int sl = sides[q].y - sides[q].x;
+                    if (sl > QS_SMALL) stack[top++] = sides[q];
+                    else if (sl > 1) small[nsmall++] = sides[q];
+                }
+            }
+            __syncthreads();
+        }
+        // short segments: insertion sort, one thread each
+        for (int q = tid; q < nsmall; q += THREADS) {
+            const int lo = small[q].x, hi = small[q].y;
+            for (int i = lo + 1; i < hi; ++i) {
+                const K v = sk[i];
+                int j = i - 1;
+                while (j >= lo && v < sk[j]) {
+                    sk[j + 1] = sk[j];
+                    --j;
+                }
+                sk[j + 1] = v;
+            }
+        }
+        __syncthreads();
+        K *dst = ti.par ? buf_k1 : buf_k0;
+        for (int pos = tid; pos < ti.cnt; pos += THREADS) {
+            const K c = sk[pos];
+            dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
+        }
+        if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
+        __syncthreads();
+    }
+}
+
+template <class K, int THREADS, int KPT> __host__ __device__ constexpr size_t quick_smem_bytes() {
+    return 2 * sizeof(K) * THREADS * KPT + sizeof(int2) * (THREADS * KPT / QS_SMALL + 2) +
+           sizeof(int2) * THREADS * KPT + sizeof(int) * (THREADS / 32) + 16;
+}
+
 // ---------------------------------------------------------------- CTA merge of a slice
 
 // Merge src[a_lo, a_lo+na) with src[b_lo, b_lo+nb) into dst[o_lo ..), with

@@ -35,6 +35,7 @@ struct PassArgs {
     const int64_t *tpp_host;  // merge_only: tiles per pair of each round (host array)
     int oddeven_rounds;       // > 0: after the sort phase, that many compare-split rounds
                               // instead of the cross-block tree (keys only, padded blocks)
+    int local_sort;           // tile sort: 0 network + merges, 1 bubble (Fig. 2), 2 quick (Fig. 4)
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };

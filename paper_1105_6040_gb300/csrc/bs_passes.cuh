@@ -81,6 +81,29 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
                                    L.stream>>>((const K *)a.in_k, (const V *)a.in_v,
                                                (g.R & 1) ? k1 : k0, (g.R & 1) ? v1 : v0, g.n, a.codec);
         if (!L.end(L.owner, CLS_SETUP, L.stream)) return BS_ERR_CUDA;
+    } else if (!HasVal<V>::value && a.local_sort == 1) {
+        // sort phase with Fig. 2's bubble sort (odd-even transposition per tile)
+        auto kb = tile_bubble_kernel<K, THREADS, KPT>;
+        const size_t sb = sizeof(K) * T;
+        static std::atomic<int> occ_b{0};
+        if (!occ_b.load()) occ_b.store(resident_ctas(kb, THREADS, sb));
+        L.begin(L.owner, CLS_TILE_SORT, L.stream);
+        kb<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_b), THREADS, sb, L.stream>>>(
+            g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
+        if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+    } else if (!HasVal<V>::value && a.local_sort == 2) {
+        // sort phase with Fig. 4's quick sort (CTA partition per tile)
+        auto kq = tile_quick_kernel<K, THREADS, KPT>;
+        constexpr size_t sq = quick_smem_bytes<K, THREADS, KPT>();
+        static std::atomic<int> occ_q{0};
+        if (!occ_q.load()) {
+            if (!allow_smem(kq, sq)) return BS_ERR_CUDA;
+            occ_q.store(resident_ctas(kq, THREADS, sq));
+        }
+        L.begin(L.owner, CLS_TILE_SORT, L.stream);
+        kq<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_q), THREADS, sq, L.stream>>>(
+            g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
+        if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     } else {
         // sort phase: every tile of every block
         L.begin(L.owner, CLS_TILE_SORT, L.stream);

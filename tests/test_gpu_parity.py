@@ -398,3 +398,36 @@ def test_oddeven_schedule_matches_oracle(n, p):
         assert counts["merge"] == p + lv  # in-block levels, then exactly p compare-split rounds
     finally:
         s.close()
+
+
+# ------------------------------------------------------------------ local sorts of Figs. 2 and 4
+
+@pytest.mark.parametrize("local", ["bubble", "quick"])
+def test_local_sort_variants_match_oracle(local):
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    try:
+        abi.bs_set_option(s.h, "local_sort", local)
+        cases = [(W.uniform_int32(1, 1), 1), (W.uniform_int32(T + 5, 2), 1),
+                 (W.uniform_int32(3 * T - 1, 3), 3), (W.dup16_int32(2 * T + 7, 4), 2),
+                 (W.reverse_int32(T), 1), (W.sorted_int32(5000), 2),
+                 (W.normal_float32_edges(20001, 5), 4), (W.uniform_uint64(9000, 6), 2)]
+        for x, p in cases:
+            got = gpu_keys(s, x, p)
+            want, _ = oracle.sort(x, p=p, local=local if x.size <= 9000 else "merge")
+            assert np.array_equal(_bits(got), _bits(want)), (local, x.dtype, x.size, p)
+        lens = np.array([0, 1, 33, 4096, 5000, 2], dtype=np.int64)
+        off = W.offsets_from_lengths(lens)
+        k = W.uniform_int32(int(off[-1]), 7) % 50
+        res = s.sort_segmented(_to_dev(k), torch.from_numpy(off).cuda())
+        s.sync()
+        assert np.array_equal(_to_host(res), oracle.sort_segmented(k, off)[0])
+        # pair sorts ignore the option and stay stable
+        kk, vv = W.uniform_uint64(7000, 8) % np.uint64(9), W.index_payload(7000)
+        ko, vo = s.sort_pairs(_to_dev(kk), _to_dev(vv), p=2)
+        s.sync()
+        wk, wv = oracle.sort(kk, vv, p=2)
+        assert np.array_equal(_to_host(ko), wk) and np.array_equal(_to_host(vo), wv)
+    finally:
+        s.close()
