@@ -251,8 +251,11 @@ typedef enum {
                                 so that CTA's bounded waits run out and the call ends
                                 with BS_ERR_TIMEOUT (and an incomplete output) */
     BS_OPT_MERGE_SCHEDULE = 5,/* value: a bs_schedule (bs_sort_keys only) */
-    BS_OPT_LOCAL_SORT = 6    /* value: a bs_local_sort (keys-only sorts; pair sorts always
+    BS_OPT_LOCAL_SORT = 6,   /* value: a bs_local_sort (keys-only sorts; pair sorts always
                                 use the stable MERGE tile sort) */
+    BS_OPT_MERGE_TILE_LOG2 = 7 /* merge-pass tile 2^value keys: 0 (default) = the sort tile,
+                                or 11 .. the sort tile's log2; smaller merge tiles use less
+                                shared memory, so more CTAs fit per SM */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

@@ -168,6 +168,7 @@ struct bs_handle {
     int withhold = 0;      // test hook (BS_OPT_TEST_WITHHOLD)
     int schedule = BS_SCHEDULE_TREE;
     int local_sort = BS_LOCAL_MERGE;
+    int merge_tile_log2 = 0;  // 0: the sort tile
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -248,6 +249,8 @@ WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs, int64_t extra_til
     L.bsum = take((size_t)((S + 1) / SCAN_BLOCK + 2) * 8);
     int64_t xt = xblock_tiles_max(n, S, 11);
     if (extra_tiles > xt) xt = extra_tiles;
+    const int64_t seg_merge_tiles = ((n + MIN_TILE - 1) / MIN_TILE + S) * 4;  // merge tiles >= 2^11
+    if (seg_merge_tiles > xt) xt = seg_merge_tiles;
     L.tseg = take((size_t)ub * 4);
     L.split = take((size_t)((ub > xt ? ub : xt) + 1) * 8);
     L.total = o;
@@ -429,6 +432,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.merge_vt = h->merge_vt;
     a.oddeven_rounds = oddeven ? (int)p : 0;
     a.local_sort = h->local_sort;
+    a.merge_tile_log2 = h->merge_tile_log2;
     st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
     if (st != BS_OK || !oddeven) return st;
     // after p rounds the keys are in buffer (p & 1): decode the first n
@@ -612,7 +616,8 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
             longest = std::max(longest, b - a);
         }
         tpp[r] = std::max<int64_t>(1, (longest + T - 1) / T);
-        need = std::max(need, ((runs + G - 1) / G) * tpp[r]);
+        // merge tiles may be up to 4x smaller than sort tiles
+        need = std::max(need, ((runs + G - 1) / G) * tpp[r] * 4);
     }
     const WsLayout W = ws_layout(n, runs, (size_t)kw, (size_t)vw, need);
     bs_status st = ensure_ws(h, W.total);
@@ -655,6 +660,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.tpp_host = tpp.data();
     a.oddeven_rounds = 0;
     a.local_sort = 0;
+    a.merge_tile_log2 = h->merge_tile_log2;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -803,6 +809,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value < BS_LOCAL_MERGE || value > BS_LOCAL_QUICK) return BS_ERR_INVALID_ARG;
         h->local_sort = (int)value;
         return BS_OK;
+    case BS_OPT_MERGE_TILE_LOG2:
+        if (value != 0 && (value < 11 || value > 13)) return BS_ERR_INVALID_ARG;
+        h->merge_tile_log2 = (int)value;
+        return BS_OK;
     case BS_OPT_MERGE_SCHEDULE:
         if (value != BS_SCHEDULE_TREE && value != BS_SCHEDULE_ODDEVEN) return BS_ERR_INVALID_ARG;
         h->schedule = (int)value;
@@ -856,6 +866,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->merge_vt = h->merge_vt;
     g->h->schedule = h->schedule;
     g->h->local_sort = h->local_sort;
+    g->h->merge_tile_log2 = h->merge_tile_log2;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

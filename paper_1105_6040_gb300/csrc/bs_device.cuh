@@ -726,8 +726,10 @@ struct Level {
     int kind;
     int lv;          // LEVEL_SEG: level
     int r;           // LEVEL_XBLOCK / LEVEL_ODDEVEN: round
-    int64_t tpp;     // LEVEL_XBLOCK: tiles per pair
-    int64_t ntiles;  // LEVEL_XBLOCK: npairs * tpp (LEVEL_SEG reads the tile count)
+    int64_t tpp;     // LEVEL_XBLOCK / LEVEL_ODDEVEN: tiles per pair
+    int64_t ntiles;  // LEVEL_XBLOCK / LEVEL_ODDEVEN: npairs * tpp (LEVEL_SEG reads the tile count)
+    int mlogT;       // merge tile = 2^mlogT keys (<= the sort tile; LEVEL_SEG cuts every sort
+                     // tile into 2^(logT - mlogT) merge tiles)
 };
 
 struct TilePair {
@@ -740,16 +742,19 @@ struct TilePair {
 __device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int64_t t) {
     TilePair p;
     const int64_t T = int64_t(1) << g.logT;
+    const int64_t TM = int64_t(1) << L.mlogT;
     if (L.kind == LEVEL_SEG) {
-        const int64_t s = g.tseg[t];
+        const int sh = g.logT - L.mlogT;
+        const int64_t ts = t >> sh, h = t & ((int64_t(1) << sh) - 1);
+        const int64_t s = g.tseg[ts];
         int64_t slo, shi;
         seg_bounds(g, s, slo, shi);
         const int Ls = seg_levels(shi - slo, g.logT);
-        const int64_t j = t - g.tprefix[s];
+        const int64_t j = ts - g.tprefix[s];
         const int64_t W = T << L.lv;
-        p.active = L.lv < Ls;
-        p.x0 = slo + j * T;
-        p.x1 = min(p.x0 + T, shi);
+        p.x0 = slo + j * T + h * TM;
+        p.x1 = min(p.x0 + TM, shi);
+        p.active = L.lv < Ls && p.x0 < shi;
         p.ps = slo + (j >> (L.lv + 1)) * 2 * W;
         p.pm = min(p.ps + W, shi);
         p.pe = min(p.ps + 2 * W, shi);
@@ -768,8 +773,8 @@ __device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int6
         p.ps = clamp64(g.off[min(first, g.S)], 0, g.n);
         p.pe = clamp64(g.off[last], p.ps, g.n);
         p.pm = last - first >= 2 ? clamp64(g.off[first + 1], p.ps, p.pe) : p.pe;
-        p.x0 = p.ps + j * T;
-        p.x1 = min(p.x0 + T, p.pe);
+        p.x0 = p.ps + j * TM;
+        p.x1 = min(p.x0 + TM, p.pe);
         p.active = p.x0 < p.pe;
         p.src = L.r & 1;
         p.dst = (L.r + 1) & 1;
@@ -780,8 +785,8 @@ __device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int6
         p.ps = clamp64(g.off[min(k * G, g.S)], 0, g.n);
         p.pm = clamp64(g.off[min(k * G + H, g.S)], p.ps, g.n);
         p.pe = clamp64(g.off[min(k * G + G, g.S)], p.pm, g.n);
-        p.x0 = p.ps + j * T;
-        p.x1 = min(p.x0 + T, p.pe);
+        p.x0 = p.ps + j * TM;
+        p.x1 = min(p.x0 + TM, p.pe);
         p.active = p.x0 < p.pe;
         p.src = (g.R - L.r) & 1;
         p.dst = (g.R - L.r - 1) & 1;
@@ -792,7 +797,7 @@ __device__ __forceinline__ TilePair tile_pair(const Geo &g, const Level &L, int6
 
 __device__ __forceinline__ int64_t level_tiles(const Geo &g, const Level &L,
                                                const int64_t *ntiles_total) {
-    return L.kind == LEVEL_SEG ? min(*ntiles_total, g.ntiles_ub) : L.ntiles;
+    return L.kind == LEVEL_SEG ? min(*ntiles_total, g.ntiles_ub) << (g.logT - L.mlogT) : L.ntiles;
 }
 
 // Merge-path split (absolute A index) at the start of every active tile.
@@ -812,15 +817,23 @@ __global__ void partition_kernel(Geo g, Level L, const K *buf0, const K *buf1, i
 }
 
 // The A and B slices of tile t: A[a_lo, a_hi), B[b_lo, b_hi) -> out[x0, x1).
+// For sorted runs the splits are monotone and these are exact.  Runs that
+// are not sorted (a caller's bad input, or malformed segment offsets) make
+// the splits arbitrary; the clamps then keep both slices inside their runs
+// and their total within the tile (x1 - x0), so the output is undefined but
+// no memory outside the arrays or the staging buffers is touched.
 struct Slice {
     int64_t a_lo, a_hi, b_lo, b_hi;
 };
 __device__ __forceinline__ Slice tile_slice(const TilePair &p, const int64_t *split, int64_t t) {
     Slice q;
-    q.a_lo = split[t];
-    q.a_hi = (p.x1 == p.pe) ? p.pm : split[t + 1];
-    q.b_lo = p.pm + (p.x0 - p.ps) - (q.a_lo - p.ps);
-    q.b_hi = p.pm + (p.x1 - p.ps) - (q.a_hi - p.ps);
+    const int64_t len = p.x1 - p.x0;
+    q.a_lo = clamp64(split[t], p.ps, p.pm);
+    const int64_t a_hi = (p.x1 == p.pe) ? p.pm : split[t + 1];
+    q.a_hi = clamp64(a_hi, q.a_lo, min(p.pm, q.a_lo + len));
+    q.b_lo = clamp64(p.pm + (p.x0 - p.ps) - (q.a_lo - p.ps), p.pm, p.pe);
+    const int64_t nb = min(len - (q.a_hi - q.a_lo), p.pe - q.b_lo);
+    q.b_hi = q.b_lo + (nb > 0 ? nb : 0);
     return q;
 }
 

@@ -36,6 +36,7 @@ struct PassArgs {
     int oddeven_rounds;       // > 0: after the sort phase, that many compare-split rounds
                               // instead of the cross-block tree (keys only, padded blocks)
     int local_sort;           // tile sort: 0 network + merges, 1 bubble (Fig. 2), 2 quick (Fig. 4)
+    int merge_tile_log2;      // merge-pass tile (0: the sort tile; else 11 .. logT)
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };

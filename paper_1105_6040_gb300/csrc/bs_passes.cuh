@@ -1,6 +1,8 @@
 // bs_passes.cuh -- host-side launch sequence of one sort (templated on the
-// key code type, value type and tile shape); instantiated per key width in
-// bs_u32.cu / bs_u64.cu.
+// key code type and value type); instantiated per key width in bs_u32.cu /
+// bs_u64.cu.  The sort phase's tile shape (THREADS x KPT keys) and the merge
+// passes' tile shape (MT x MVT keys, at most the sort tile) are chosen
+// independently.
 #pragma once
 
 #include <atomic>
@@ -30,49 +32,83 @@ static inline int64_t grid_for(int64_t work, int64_t resident) {
 // Shared memory a CTA may use while still leaving room for a second CTA.
 constexpr size_t TMA_SMEM_AUTO_LIMIT = 112 * 1024;
 constexpr size_t SMEM_OPT_IN_LIMIT = 227 * 1024;
+constexpr int PART_THREADS = 256;  // partition threads per CTA
 
-template <class K, class V, int THREADS, int KPT>
-bs_status run_passes_t(const PassArgs &a, Launcher &L) {
-    constexpr int T = THREADS * KPT;
+// One merge pass with merge tiles of MT x MVT keys: merge-path splits, then
+// the TMA pipeline (when allowed and it fits) or the plain kernel.
+template <class K, class V, int MT, int MVT>
+bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
     constexpr int STAGES = 2;
-    const size_t smem = smem_bytes<K, V>(T);
-    const size_t tsmem = tile_smem_bytes<K, V>(T);
-    constexpr size_t msmem = tma_smem_bytes<K, V, THREADS, KPT, STAGES>();
-    // wide consumer shape: twice the threads, half the keys each, same tile
-    constexpr bool HAS_WIDE = 2 * THREADS + 32 <= 1024;
-    constexpr int WT = HAS_WIDE ? 2 * THREADS : THREADS, WVT = HAS_WIDE ? KPT / 2 : KPT;
-    constexpr size_t wsmem = tma_smem_bytes<K, V, WT, WVT, STAGES>();
-    auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
-    auto mk = merge_kernel<K, V, THREADS, KPT>;
-    auto mt = merge_tma_kernel<K, V, THREADS, KPT, STAGES>;
-    auto mw = merge_tma_kernel<K, V, WT, WVT, STAGES>;
+    constexpr int TM = MT * MVT;
+    constexpr size_t smem = smem_bytes<K, V>(TM);
+    constexpr size_t msmem = tma_smem_bytes<K, V, MT, MVT, STAGES>();
+    auto mk = merge_kernel<K, V, MT, MVT>;
+    auto mt = merge_tma_kernel<K, V, MT, MVT, STAGES>;
     auto pk = partition_kernel<K>;
-    // per-instantiation launch shapes, computed once (idempotent, so a race
-    // between host threads only repeats the same work)
-    static std::atomic<int> occ_ts{0}, occ_mk{0}, occ_mt{0}, occ_mw{0};
-    if (!occ_ts.load()) {
-        if (!allow_smem(ts, tsmem) || !allow_smem(mk, smem)) return BS_ERR_CUDA;
-        occ_mk.store(resident_ctas(mk, THREADS, smem));
+    static std::atomic<int> occ_mk{0}, occ_mt{0};
+    if (!occ_mk.load()) {
+        if (!allow_smem(mk, smem)) return false;
         if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem))
-            occ_mt.store(resident_ctas(mt, THREADS + 32, msmem));
+            occ_mt.store(resident_ctas(mt, MT + 32, msmem));
         else
             occ_mt.store(-1);
-        if (HAS_WIDE && wsmem <= SMEM_OPT_IN_LIMIT && allow_smem(mw, wsmem))
-            occ_mw.store(resident_ctas(mw, WT + 32, wsmem));
-        else
-            occ_mw.store(-1);
-        occ_ts.store(resident_ctas(ts, THREADS, tsmem));
+        occ_mk.store(resident_ctas(mk, MT, smem));
     }
     bool tma = false;
     if (occ_mt.load() > 0) {
         if (a.merge_impl == MERGE_TMA) tma = true;
         else if (a.merge_impl == MERGE_AUTO) tma = msmem <= TMA_SMEM_AUTO_LIMIT;
     }
-    const bool wide = tma && a.merge_vt == 8 && occ_mw.load() > 0;
+    (void)TM;
     const Geo &g = a.g;
     K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
     V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
-    const int PT = 256;  // partition threads per CTA
+    L.begin(L.owner, CLS_PARTITION, L.stream);
+    pk<<<(unsigned)grid_for((tiles + PART_THREADS - 1) / PART_THREADS, (int64_t)L.sms * 8), PART_THREADS,
+         0, L.stream>>>(g, lvl, k0, k1, a.split, a.ntiles_total);
+    if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
+    L.begin(L.owner, CLS_MERGE, L.stream);
+    if (tma)
+        mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt), MT + 32, msmem, L.stream>>>(
+            g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+    else
+        mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream>>>(
+            g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
+    return L.end(L.owner, CLS_MERGE, L.stream);
+}
+
+// Merge-pass shapes: (merge tile log2, keys per consumer thread).  The plain
+// kernel always runs 16 keys per thread.
+template <class K, class V>
+bool merge_pass_any(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
+    const bool vt8 = a.merge_vt == 8 && a.merge_impl != MERGE_SIMPLE;
+    switch (lvl.mlogT) {
+    case 11:
+        return vt8 ? merge_pass<K, V, 256, 8>(a, L, lvl, tiles) : merge_pass<K, V, 128, 16>(a, L, lvl, tiles);
+    case 12:
+        return vt8 ? merge_pass<K, V, 512, 8>(a, L, lvl, tiles) : merge_pass<K, V, 256, 16>(a, L, lvl, tiles);
+    case 13: return merge_pass<K, V, 512, 16>(a, L, lvl, tiles);
+    default: return false;
+    }
+}
+
+template <class K, class V, int THREADS, int KPT>
+bs_status run_passes_t(const PassArgs &a, Launcher &L) {
+    constexpr int T = THREADS * KPT;
+    const size_t tsmem = tile_smem_bytes<K, V>(T);
+    auto ts = tile_sort_kernel<K, V, THREADS, KPT>;
+    static std::atomic<int> occ_ts{0};
+    if (!occ_ts.load()) {
+        if (!allow_smem(ts, tsmem)) return BS_ERR_CUDA;
+        occ_ts.store(resident_ctas(ts, THREADS, tsmem));
+    }
+    const Geo &g = a.g;
+    K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
+    V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
+    // merge tile: at most the sort tile (the plain kernel always uses the sort tile)
+    int mlogT = a.merge_tile_log2 ? a.merge_tile_log2 : g.logT;
+    if (mlogT > g.logT || mlogT < 11 || a.merge_impl == MERGE_SIMPLE) mlogT = g.logT;
+    const int64_t TM = int64_t(1) << mlogT;
 
     if (a.merge_only) {
         // runs arrive sorted: encode them into the buffer the rounds start from
@@ -112,52 +148,35 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     }
 
-    // one merge pass: merge-path splits, then the merge kernel
-    auto pass = [&](const Level &lvl, int64_t tiles) -> bool {
-        L.begin(L.owner, CLS_PARTITION, L.stream);
-        pk<<<(unsigned)grid_for((tiles + PT - 1) / PT, (int64_t)L.sms * 8), PT, 0, L.stream>>>(
-            g, lvl, k0, k1, a.split, a.ntiles_total);
-        if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
-        L.begin(L.owner, CLS_MERGE, L.stream);
-        if (wide)
-            mw<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mw), WT + 32, wsmem, L.stream>>>(
-                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-        else if (tma)
-            mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt), THREADS + 32, msmem, L.stream>>>(
-                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-        else
-            mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), THREADS, smem, L.stream>>>(
-                g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-        return L.end(L.owner, CLS_MERGE, L.stream);
-    };
-
     // sort phase, continued: in-block merge levels
     for (int lv = 0; lv < a.Lmax; ++lv) {
-        Level lvl{LEVEL_SEG, lv, 0, 0, 0};
-        if (!pass(lvl, a.ntiles_ub)) return BS_ERR_CUDA;
+        Level lvl{LEVEL_SEG, lv, 0, 0, 0, mlogT};
+        if (!merge_pass_any<K, V>(a, L, lvl, a.ntiles_ub << (g.logT - mlogT))) return BS_ERR_CUDA;
     }
+
     // merge phase, odd-even form: compare-split rounds over equal blocks
     if (a.oddeven_rounds > 0) {
         const int64_t cap = g.n / g.S;
-        const int64_t tpp = (2 * cap + T - 1) / T;
+        const int64_t tpp = (2 * cap + TM - 1) / TM;
         for (int r = 0; r < a.oddeven_rounds; ++r) {
-            Level lvl{LEVEL_ODDEVEN, 0, r, tpp, 0};
+            Level lvl{LEVEL_ODDEVEN, 0, r, tpp, 0, mlogT};
             const int64_t npairs = (r & 1) ? 1 + g.S / 2 : (g.S + 1) / 2;
             lvl.ntiles = npairs * tpp;
-            if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
+            if (!merge_pass_any<K, V>(a, L, lvl, lvl.ntiles)) return BS_ERR_CUDA;
         }
         return BS_OK;
     }
     // merge phase: cross-block rounds, tiles aligned to each pair's start
     for (int r = 0; r < g.R; ++r) {
-        Level lvl{LEVEL_XBLOCK, 0, r, 0, 0};
+        Level lvl{LEVEL_XBLOCK, 0, r, 0, 0, mlogT};
         if (a.tpp_host) {
-            lvl.tpp = a.tpp_host[r];
+            // runs given by the caller: tiles per pair from their lengths (in sort tiles)
+            lvl.tpp = a.tpp_host[r] << (g.logT - mlogT);
             lvl.ntiles = ((g.S + (int64_t(2) << r) - 1) >> (r + 1)) * lvl.tpp;
         } else {
-            lvl.ntiles = xblock_tiles(g.n, g.S, r, g.logT, &lvl.tpp);
+            lvl.ntiles = xblock_tiles(g.n, g.S, r, mlogT, &lvl.tpp);
         }
-        if (!pass(lvl, lvl.ntiles)) return BS_ERR_CUDA;
+        if (!merge_pass_any<K, V>(a, L, lvl, lvl.ntiles)) return BS_ERR_CUDA;
     }
     return BS_OK;
 }
@@ -179,7 +198,7 @@ bs_status oddeven_compact_t(const void *in, void *out, int64_t n, int codec, Lau
     return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
 }
 
-// Dispatch on the value width and the tile shape (T = 2^logT = THREADS*16).
+// Dispatch on the value width and the sort tile shape (T = 2^logT = THREADS*16).
 template <class K, class V> bs_status run_passes_v(const PassArgs &a, Launcher &L) {
     switch (a.g.logT) {
     case 11: return run_passes_t<K, V, 128, 16>(a, L);

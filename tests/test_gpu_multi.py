@@ -70,3 +70,23 @@ def test_exchange_sort_one_rank_on_gpu(sorter):
         assert keys == x.size and ms == 2.0
     finally:
         dist.destroy_process_group()
+
+
+def test_unsorted_runs_and_overlapping_offsets_stay_in_bounds(sorter):
+    """Inputs that break the sortedness a merge pass relies on (runs that are
+    not sorted; overlapping segment offsets spanning many tiles) give an
+    undefined output but no fault, and the handle keeps working."""
+    from paper_1105_6040_gb300 import abi
+    x = W.uniform_int32(1 << 18, seed=11)
+    d = torch.from_numpy(x).cuda()
+    for tma in ("tma", "simple"):
+        abi.bs_set_option(sorter.h, "merge_kernel", tma)
+        sorter.merge_runs(d, [0, 100003, 150000, 1 << 18])  # runs not sorted
+        sorter.sync()
+        bad = torch.tensor([0, 150000, 50000, 1 << 18], dtype=torch.int64, device="cuda")
+        sorter.sort_segmented(d, bad)
+        assert abi.bs_sync_status(sorter.h) == abi.BS_ERR_INVALID_ARG
+        out = sorter.sort_keys(d, p=3)
+        sorter.sync()
+        assert np.array_equal(out.cpu().numpy(), np.sort(x))
+    abi.bs_set_option(sorter.h, "merge_kernel", "auto")
