@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--per-array-rounds", type=int, default=2)
     ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16])
     ap.add_argument("--merge-tile-log2", type=int, default=0, choices=[0, 11, 12, 13])
+    ap.add_argument("--merge-consumer", type=int, default=0, choices=[0, 1])
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--streams", type=int, default=4, help="serving: execution slots")
@@ -191,6 +192,7 @@ def config(args):
             "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
             "merge_kernel": args.merge, "merge_vt": args.merge_vt or 16,
             "merge_tile_keys": 1 << (args.merge_tile_log2 or args.tile_log2),
+            "merge_consumer": ["warp", "thread"][args.merge_consumer],
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
             "stream": "torch current stream", "out_of_place": True}
 
@@ -279,7 +281,8 @@ def run_ours(args):
     cpu_sample = keys_h[: 1 << min(args.cpu_sample_log2, args.log2n)].copy()
 
     sorter = abi.Sorter(local, tile_log2=args.tile_log2, merge_kernel=args.merge,
-                        merge_vt=args.merge_vt, merge_tile_log2=args.merge_tile_log2)
+                        merge_vt=args.merge_vt, merge_tile_log2=args.merge_tile_log2,
+                        merge_consumer=args.merge_consumer)
     d_in = torch.from_numpy(keys_h).cuda()
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()

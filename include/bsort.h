@@ -253,9 +253,12 @@ typedef enum {
     BS_OPT_MERGE_SCHEDULE = 5,/* value: a bs_schedule (bs_sort_keys only) */
     BS_OPT_LOCAL_SORT = 6,   /* value: a bs_local_sort (keys-only sorts; pair sorts always
                                 use the stable MERGE tile sort) */
-    BS_OPT_MERGE_TILE_LOG2 = 7 /* merge-pass tile 2^value keys: 0 (default) = the sort tile,
+    BS_OPT_MERGE_TILE_LOG2 = 7,/* merge-pass tile 2^value keys: 0 (default) = the sort tile,
                                 or 11 .. the sort tile's log2; smaller merge tiles use less
                                 shared memory, so more CTAs fit per SM */
+    BS_OPT_MERGE_CONSUMER = 8 /* TMA merge consumers: 0 (default) each warp merges a slice with
+                                a bitonic merger over registers and shuffles; 1 each thread
+                                finds its own merge-path split and merges VT candidates */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

@@ -191,7 +191,8 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
 
 
 OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2, "wait_limit_ms": 3,
-           "test_withhold": 4, "merge_schedule": 5, "local_sort": 6, "merge_tile_log2": 7}
+           "test_withhold": 4, "merge_schedule": 5, "local_sort": 6, "merge_tile_log2": 7,
+           "merge_consumer": 8}
 SCHEDULES = {"tree": 0, "oddeven": 1}
 LOCAL_SORTS = {"merge": 0, "bubble": 1, "quick": 2}
 MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}
@@ -284,7 +285,7 @@ class Sorter:
     """A library handle on one CUDA device, taking torch tensors."""
 
     def __init__(self, device=None, tile_log2: int = 0, merge_kernel: str = "auto",
-                 merge_vt: int = 0, merge_tile_log2: int = 0):
+                 merge_vt: int = 0, merge_tile_log2: int = 0, merge_consumer: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Sorter needs a CUDA device; there is no CPU path")
@@ -299,6 +300,8 @@ class Sorter:
             bs_set_option(self.h, "merge_vt", merge_vt)
         if merge_tile_log2:
             bs_set_option(self.h, "merge_tile_log2", merge_tile_log2)
+        if merge_consumer:
+            bs_set_option(self.h, "merge_consumer", merge_consumer)
 
     def close(self):
         if getattr(self, "h", None):

@@ -169,6 +169,7 @@ struct bs_handle {
     int schedule = BS_SCHEDULE_TREE;
     int local_sort = BS_LOCAL_MERGE;
     int merge_tile_log2 = 0;  // 0: the sort tile
+    int merge_consumer = 0;   // 0 warp bitonic merger, 1 per-thread candidate merge
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -249,7 +250,9 @@ WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs, int64_t extra_til
     L.bsum = take((size_t)((S + 1) / SCAN_BLOCK + 2) * 8);
     int64_t xt = xblock_tiles_max(n, S, 11);
     if (extra_tiles > xt) xt = extra_tiles;
-    const int64_t seg_merge_tiles = ((n + MIN_TILE - 1) / MIN_TILE + S) * 4;  // merge tiles >= 2^11
+    // in-block levels launch (n / T + S + 1) << (logT - mlogT) merge tiles, with
+    // 2^11 <= 2^mlogT <= T <= 2^13: at most n / 2^11 + 4 (S + 1)
+    const int64_t seg_merge_tiles = (n + MIN_TILE - 1) / MIN_TILE + 4 * (S + 1);
     if (seg_merge_tiles > xt) xt = seg_merge_tiles;
     L.tseg = take((size_t)ub * 4);
     L.split = take((size_t)((ub > xt ? ub : xt) + 1) * 8);
@@ -433,6 +436,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.oddeven_rounds = oddeven ? (int)p : 0;
     a.local_sort = h->local_sort;
     a.merge_tile_log2 = h->merge_tile_log2;
+    a.merge_consumer = h->merge_consumer;
     st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
     if (st != BS_OK || !oddeven) return st;
     // after p rounds the keys are in buffer (p & 1): decode the first n
@@ -661,6 +665,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.oddeven_rounds = 0;
     a.local_sort = 0;
     a.merge_tile_log2 = h->merge_tile_log2;
+    a.merge_consumer = h->merge_consumer;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -813,6 +818,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value != 0 && (value < 11 || value > 13)) return BS_ERR_INVALID_ARG;
         h->merge_tile_log2 = (int)value;
         return BS_OK;
+    case BS_OPT_MERGE_CONSUMER:
+        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        h->merge_consumer = (int)value;
+        return BS_OK;
     case BS_OPT_MERGE_SCHEDULE:
         if (value != BS_SCHEDULE_TREE && value != BS_SCHEDULE_ODDEVEN) return BS_ERR_INVALID_ARG;
         h->schedule = (int)value;
@@ -867,6 +876,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->schedule = h->schedule;
     g->h->local_sort = h->local_sort;
     g->h->merge_tile_log2 = h->merge_tile_log2;
+    g->h->merge_consumer = h->merge_consumer;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -1001,6 +1001,93 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
     return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) + 128;
 }
 
+// Warp consumer of one staged tile: warp w produces outputs [d0, d1) of the
+// tile (32*VT of them).  Lanes 0 and 1 find the merge-path splits at d0 and
+// d1; the warp then reads its A slice followed by its B slice reversed --
+// a bitonic sequence, padded in the middle with the largest key -- striped
+// across lanes (element e at lane e%32, register e/32: conflict-free shared
+// loads), sorts it with a bitonic merger (register strides, then shuffle
+// strides 16..1) and stores it coalesced.  Pairs compare (key, staging index)
+// and fetch their values at the end.
+template <class K, class V, int VT>
+__device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const V *sav, const V *sbv,
+                                                int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
+                                                int codec, uint64_t *empty_bar, int tid) {
+    constexpr bool HV = HasVal<V>::value;
+    constexpr int WO = 32 * VT;
+    const int lane = tid & 31, w = tid >> 5;
+    const int total = na + nb;
+    const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
+    int sp = 0;
+    if (lane < 2) {
+        const int dd = lane ? d1 : d0;
+        sp = merge_path_pred<int>(na, nb, dd, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
+    }
+    const int i0 = __shfl_sync(0xffffffffu, sp, 0), i1 = __shfl_sync(0xffffffffu, sp, 1);
+    const int naw = i1 - i0, j0 = d0 - i0, nbw = (d1 - d0) - naw;
+    K v[VT];
+    uint32_t x[VT];
+#pragma unroll
+    for (int k = 0; k < VT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < naw) {
+            v[k] = sa[i0 + e];
+            x[k] = (uint32_t)(i0 + e);
+        } else if (e >= WO - nbw) {
+            const int bi = j0 + (WO - 1 - e);
+            v[k] = sb[bi];
+            x[k] = (uint32_t)(na + bi);
+        } else {
+            v[k] = max_code<K>();
+            x[k] = 0xffffffffu;
+        }
+    }
+    if constexpr (!HV) mbar_arrive(empty_bar);  // every shared read of this stage is done
+    // bitonic merger: register strides WO/2 .. 32, then lane strides 16 .. 1
+#pragma unroll
+    for (int r = VT >> 1; r > 0; r >>= 1) {
+#pragma unroll
+        for (int k = 0; k < VT; ++k) {
+            if ((k & r) == 0) {
+                if constexpr (HV) cas_pairs(v[k], x[k], v[k + r], x[k + r]);
+                else cas_keys(v[k], v[k + r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int ls = 16; ls > 0; ls >>= 1) {
+        const bool up = lane & ls;
+#pragma unroll
+        for (int k = 0; k < VT; ++k) {
+            const K pk = shfl_xor_k<VT>(v[k], ls);
+            if constexpr (HV) {
+                const uint32_t px = __shfl_xor_sync(0xffffffffu, x[k], ls);
+                const bool take = up ? ki_less(v[k], x[k], pk, px) : ki_less(pk, px, v[k], x[k]);
+                v[k] = take ? pk : v[k];
+                x[k] = take ? px : x[k];
+            } else {
+                v[k] = up ? (v[k] < pk ? pk : v[k]) : (v[k] < pk ? v[k] : pk);
+            }
+        }
+    }
+    V vals[VT];
+    if constexpr (HV) {
+#pragma unroll
+        for (int k = 0; k < VT; ++k)
+            if (lane + 32 * k < d1 - d0) vals[k] = (int)x[k] < na ? sav[x[k]] : sbv[x[k] - na];
+        mbar_arrive(empty_bar);
+    }
+    K *out = dk + o_lo + d0;
+#pragma unroll
+    for (int k = 0; k < VT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < d1 - d0) {
+            out[e] = fin ? dec_code(v[k], codec) : v[k];
+            if constexpr (HV) dv[o_lo + d0 + e] = vals[k];
+        }
+    }
+}
+
 // Merge pass with a TMA pipeline (warp specialised, persistent).  The last
 // warp produces: for each of this CTA's tiles it computes the A and B slices
 // and stages them by 1-D bulk copies into a ring of STAGES shared-memory
@@ -1008,7 +1095,7 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
 // merge-path split, candidate merge of VT outputs per thread, 16-byte
 // vector stores straight to the output.  All waits are bounded; a timeout
 // records BS_ERR_TIMEOUT and ends the CTA.  Needs 16-byte aligned buffers.
-template <class K, class V, int THREADS, int VT, int STAGES>
+template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE>
 __global__ void __launch_bounds__(THREADS + 32)
 merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
                  const int64_t *__restrict__ split, const int64_t *__restrict__ ntiles_total) {
@@ -1098,6 +1185,15 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             const K *sa = stage_a(s) + d.a_off;
             const K *sb = stage_b(s) + d.b_off;
             const int na = d.na, nb = d.nb, total_out = na + nb;
+            if constexpr (WARPMERGE) {
+                warp_merge_tile<K, V, VT>(sa, sb, stage_av(s) + d.av_off, stage_bv(s) + d.bv_off, na, nb,
+                                          (d.flags & 2) ? buf_k1 : buf_k0, (d.flags & 2) ? buf_v1 : buf_v0,
+                                          d.o_lo, (d.flags & 4) != 0, codec, &empty[s], tid);
+                if (tid == 0)
+                    atomicAdd(g.counters + CLS_MERGE,
+                              2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
+                continue;
+            }
             const int diag = min(tid * VT, total_out);
             const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
             const int j = diag - i;

@@ -201,6 +201,7 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     a.oddeven_rounds = 0;
     a.local_sort = 0;
     a.merge_tile_log2 = 0;
+    a.merge_consumer = 0;
     bs::Launcher L{s, nullptr, sms, no_begin, check_end};
     return kw == 4 ? bs::run_passes_u32(a, L) : bs::run_passes_u64(a, L);
 }

@@ -43,19 +43,23 @@ bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles)
     constexpr size_t smem = smem_bytes<K, V>(TM);
     constexpr size_t msmem = tma_smem_bytes<K, V, MT, MVT, STAGES>();
     auto mk = merge_kernel<K, V, MT, MVT>;
-    auto mt = merge_tma_kernel<K, V, MT, MVT, STAGES>;
+    auto mt = a.merge_consumer == 1 ? merge_tma_kernel<K, V, MT, MVT, STAGES, false>
+                                    : merge_tma_kernel<K, V, MT, MVT, STAGES, true>;
     auto pk = partition_kernel<K>;
-    static std::atomic<int> occ_mk{0}, occ_mt{0};
+    static std::atomic<int> occ_mk{0}, occ_mt[2] = {{0}, {0}};
+    const int ci = a.merge_consumer == 1 ? 1 : 0;
     if (!occ_mk.load()) {
         if (!allow_smem(mk, smem)) return false;
-        if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem))
-            occ_mt.store(resident_ctas(mt, MT + 32, msmem));
-        else
-            occ_mt.store(-1);
         occ_mk.store(resident_ctas(mk, MT, smem));
     }
+    if (!occ_mt[ci].load()) {
+        if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem))
+            occ_mt[ci].store(resident_ctas(mt, MT + 32, msmem));
+        else
+            occ_mt[ci].store(-1);
+    }
     bool tma = false;
-    if (occ_mt.load() > 0) {
+    if (occ_mt[ci].load() > 0) {
         if (a.merge_impl == MERGE_TMA) tma = true;
         else if (a.merge_impl == MERGE_AUTO) tma = msmem <= TMA_SMEM_AUTO_LIMIT;
     }
@@ -69,7 +73,7 @@ bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles)
     if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
     L.begin(L.owner, CLS_MERGE, L.stream);
     if (tma)
-        mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt), MT + 32, msmem, L.stream>>>(
+        mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt[ci]), MT + 32, msmem, L.stream>>>(
             g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
     else
         mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream>>>(

@@ -308,15 +308,17 @@ def test_2e28_int32_uniform_p2_sampled(sorter):
 
 # ------------------------------------------------------------------ merge kernels
 
-@pytest.mark.parametrize("merge_kernel,merge_vt,tile_log2,merge_tile_log2", [
-    ("simple", 0, 12, 0), ("tma", 16, 12, 0), ("tma", 8, 12, 0), ("tma", 16, 12, 11),
-    ("tma", 8, 12, 11), ("tma", 16, 13, 11), ("tma", 16, 13, 12), ("auto", 0, 11, 11)])
-def test_merge_kernel_variants(merge_kernel, merge_vt, tile_log2, merge_tile_log2):
-    """Every merge-pass kernel and merge-tile shape gives the oracle's output
-    on every key/value type, ragged sizes, several p and segmented inputs."""
+@pytest.mark.parametrize("merge_kernel,merge_vt,tile_log2,merge_tile_log2,consumer", [
+    ("simple", 0, 12, 0, 0), ("tma", 16, 12, 0, 0), ("tma", 8, 12, 0, 0), ("tma", 16, 12, 11, 0),
+    ("tma", 8, 12, 11, 0), ("tma", 16, 13, 11, 0), ("tma", 16, 13, 12, 0), ("auto", 0, 11, 11, 0),
+    ("tma", 16, 12, 0, 1), ("tma", 8, 13, 12, 1)])
+def test_merge_kernel_variants(merge_kernel, merge_vt, tile_log2, merge_tile_log2, consumer):
+    """Every merge-pass kernel, consumer and merge-tile shape gives the
+    oracle's output on every key/value type, ragged sizes, several p and
+    segmented inputs."""
     from paper_1105_6040_gb300.abi import Sorter
     s = Sorter(0, merge_kernel=merge_kernel, merge_vt=merge_vt, tile_log2=tile_log2,
-               merge_tile_log2=merge_tile_log2)
+               merge_tile_log2=merge_tile_log2, merge_consumer=consumer)
     try:
         for n, p in ((3 * T + 7, 1), (100003, 3), (1 << 18, 6), (262139, 64)):
             check_keys(s, W.uniform_int32(n, n + p), p)
