@@ -343,6 +343,28 @@ def test_merge_kernel_variants(merge_kernel, merge_vt, tile_log2, merge_tile_log
         s.close()
 
 
+@pytest.mark.parametrize("merge_vt,consumer", [(8, 1), (16, 1), (8, 0), (16, 0)])
+def test_merge_stage_reuse_repeated(merge_vt, consumer):
+    """Stress for the TMA pipeline's stage ring: many short segmented merges,
+    run ten times; every run must equal the oracle.  A consumer read that is
+    not ordered before the bulk copy refilling its stage corrupts keys here
+    (fast consumers, a producer that refills at once)."""
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0, merge_kernel="tma", merge_vt=merge_vt, tile_log2=12, merge_consumer=consumer)
+    try:
+        lens = W.loguniform_lengths(400, 1, 1 << 15, seed=77)
+        off = W.offsets_from_lengths(lens)
+        k = W.uniform_int32(int(off[-1]), seed=78)
+        want = oracle.sort_segmented(k, off)[0]
+        dk, doff = _to_dev(k), torch.from_numpy(off).cuda()
+        for _ in range(10):
+            res = s.sort_segmented(dk, doff)
+            s.sync()
+            assert np.array_equal(_to_host(res), want)
+    finally:
+        s.close()
+
+
 def test_unaligned_buffers_fall_back(sorter):
     """Buffers that are not 16-byte aligned still sort correctly."""
     x = W.uniform_int32(50001, 88)
