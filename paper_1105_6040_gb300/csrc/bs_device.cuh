@@ -22,6 +22,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "bsort.h"
@@ -988,6 +989,14 @@ __device__ __forceinline__ int stage_window(T *dst, const T *a, int64_t n, int64
     return (int)(lo - ws);
 }
 
+// Items that stage_window(.., lo, hi, ..) occupies in shared memory, rounded
+// up to 16 bytes: where the next window may start.
+template <class T> __device__ __forceinline__ int window_span(int64_t lo, int64_t hi) {
+    constexpr int64_t E = 16 / sizeof(T);
+    if (hi <= lo) return 0;
+    return (int)(((hi - (lo & ~(E - 1))) + E - 1) & ~(E - 1));
+}
+
 // Descriptor of one staged tile, written by the producer next to its data.
 struct StageDesc {
     int64_t o_lo;
@@ -997,63 +1006,146 @@ struct StageDesc {
     int pad;
 };
 
+// One stage holds the tile's A and B windows back to back (B's starts at the
+// next 16-byte boundary after A's), so it needs the tile's size plus the
+// rounding of four window ends: TT + 6 * (16 / item size) items.
 template <class K, class V, int TT> struct TmaLayout {
-    static constexpr int WIN = TT + 32 / (int)sizeof(K) + 2;  // items per key window
-    static constexpr int WINV = TT + 32 / (int)(sizeof(V) > 1 ? sizeof(V) : 4) + 2;
-    static constexpr size_t keys = ((size_t)WIN * sizeof(K) + 127) & ~size_t(127);
+    static constexpr int EK = 16 / (int)sizeof(K);
+    static constexpr int EV = sizeof(V) > 1 ? 16 / (int)sizeof(V) : 1;
+    static constexpr size_t keys = ((size_t)(TT + 6 * EK) * sizeof(K) + 127) & ~size_t(127);
     static constexpr size_t vals =
-        sizeof(V) > 1 ? (((size_t)WINV * sizeof(V) + 127) & ~size_t(127)) : 0;
-    static constexpr size_t stage = 2 * keys + 2 * vals + 128;  // A, B windows + descriptor
+        sizeof(V) > 1 ? (((size_t)(TT + 6 * EV) * sizeof(V) + 127) & ~size_t(127)) : 0;
+    static constexpr size_t stage = keys + vals + 128;  // windows + descriptor
 };
 
-template <class K, class V, int THREADS, int VT, int STAGES>
+// Per-warp scratch of the warp consumer: the warp's 32*VT keys (and, for
+// pairs, their staging indices), in 16-byte chunks of keys stored at the
+// XOR-swizzled chunk position c ^ ((c >> 3) & 7), which keeps the striped
+// scalar writes and the 16-byte chunk reads and writes of both transposes
+// free of bank conflicts.
+template <class K, class V, int VT> struct WarpScratch {
+    static constexpr size_t keys = ((size_t)32 * VT * sizeof(K) + 127) & ~size_t(127);
+    static constexpr size_t idx = HasVal<V>::value ? (((size_t)32 * VT * 4 + 127) & ~size_t(127)) : 0;
+    static constexpr size_t bytes = keys + idx;
+};
+__device__ __forceinline__ int swz_chunk(int c) { return c ^ ((c >> 3) & 7); }
+
+// N items of T (8 or 16 bytes in all) moved as one shared-memory access.
+template <class T, int N> __device__ __forceinline__ void ld_chunk(const T *p, T *v) {
+    static_assert(sizeof(T) * N == 16 || sizeof(T) * N == 8, "chunk of 8 or 16 bytes");
+    if constexpr (sizeof(T) * N == 16) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        memcpy(v, &u, 16);
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        memcpy(v, &u, 8);
+    }
+}
+template <class T, int N> __device__ __forceinline__ void st_chunk(T *p, const T *v) {
+    static_assert(sizeof(T) * N == 16 || sizeof(T) * N == 8, "chunk of 8 or 16 bytes");
+    if constexpr (sizeof(T) * N == 16) {
+        uint4 u;
+        memcpy(&u, v, 16);
+        *reinterpret_cast<uint4 *>(p) = u;
+    } else {
+        uint2 u;
+        memcpy(&u, v, 8);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+}
+
+template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + 2 * STAGES * sizeof(uint64_t) + 128;
+    return STAGES * TmaLayout<K, V, THREADS * VT>::stage +
+           (WARPMERGE ? (THREADS / 32) * WarpScratch<K, V, VT>::bytes : 0) + 2 * STAGES * sizeof(uint64_t) +
+           128;
 }
 
 // Warp consumer of one staged tile: warp w produces outputs [d0, d1) of the
-// tile (32*VT of them).  Lanes 0 and 1 find the merge-path splits at d0 and
-// d1; the warp then reads its A slice followed by its B slice reversed --
-// a bitonic sequence, padded in the middle with the largest key -- striped
-// across lanes (element e at lane e%32, register e/32: conflict-free shared
-// loads), sorts it with a bitonic merger (register strides, then shuffle
-// strides 16..1) and stores it coalesced.  Pairs compare (key, staging index)
-// and fetch their values at the end.
+// tile (32*VT of them).  The warp finds the merge-path splits at d0 and d1
+// (a 17-way search per half-warp), then reads its A slice followed by its B
+// slice reversed -- a bitonic sequence, padded in the middle with the
+// largest key -- striped across lanes (element e at lane e%32, register
+// e/32: conflict-free shared loads) and sorts it with a bitonic merger: the
+// strides of 32 and more are register compare-exchanges in this layout; a
+// transpose through the warp's scratch then gives each lane VT consecutive
+// elements, so that of the strides below 32 only those of VT and more cross
+// lanes (shuffles) and the rest are register compare-exchanges again.  A
+// second transpose hands lane l the 16-byte chunks l, l+32, .. of the warp's
+// output, so that every store instruction writes 512 contiguous bytes.
+// Pairs compare (key, staging index), carry the index through both
+// transposes and fetch their values at the end.
 template <class K, class V, int VT>
 __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const V *sav, const V *sbv,
                                                 int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
-                                                int codec, uint64_t *empty_bar, int tid) {
+                                                int codec, uint64_t *empty_bar, int tid, K *wk,
+                                                uint32_t *wx) {
     constexpr bool HV = HasVal<V>::value;
     constexpr int WO = 32 * VT;
+    constexpr int E = 16 / (int)sizeof(K);  // keys per 16-byte chunk
+    constexpr int C = VT / E;               // chunks per lane
+    static_assert(C >= 1 && VT % E == 0, "whole chunks per lane");
     const int lane = tid & 31, w = tid >> 5;
     const int total = na + nb;
     const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
-    int sp = 0;
-    if (lane < 2) {
-        const int dd = lane ? d1 : d0;
-        sp = merge_path_pred<int>(na, nb, dd, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
+    // the merge-path splits at d0 (lanes 0-15) and d1 (lanes 16-31): each
+    // half-warp tests 16 evenly spaced points of the interval holding its
+    // split, whose predicate B[d-1-i] < A[i] is false then true, and keeps
+    // the piece between the last false and the first true test (17-way
+    // search: 3 rounds for a 4096-key tile)
+    int i0, i1;
+    {
+        const int half = lane >> 4, sub = lane & 15;
+        const int dd = half ? d1 : d0;
+        int lo = dd > nb ? dd - nb : 0, hi = dd < na ? dd : na;
+        while (__any_sync(0xffffffffu, lo < hi)) {
+            const bool live = lo < hi;
+            const int mid = lo + ((sub + 1) * (hi - lo)) / 17;  // lo <= mid < hi
+            const bool test = live && sb[dd - 1 - mid] < sa[mid];
+            const unsigned yes = (__ballot_sync(0xffffffffu, test) >> (16 * half)) & 0xffffu;
+            const int f = yes ? __ffs(yes) - 1 : 16;  // first point whose test holds
+            const int mprev = __shfl_sync(0xffffffffu, mid, 16 * half + (f > 0 ? f - 1 : 0));
+            const int mf = __shfl_sync(0xffffffffu, mid, 16 * half + (f < 16 ? f : 15));
+            if (live) {
+                if (f > 0) lo = mprev + 1;
+                if (f < 16) hi = mf;
+            }
+        }
+        i0 = __shfl_sync(0xffffffffu, lo, 0);
+        i1 = __shfl_sync(0xffffffffu, lo, 16);
     }
-    const int i0 = __shfl_sync(0xffffffffu, sp, 0), i1 = __shfl_sync(0xffffffffu, sp, 1);
     const int naw = i1 - i0, j0 = d0 - i0, nbw = (d1 - d0) - naw;
     K v[VT];
     uint32_t x[VT];
+    if (naw + nbw == WO) {
+        // a full warp: every element is A's or B's
+        const K *pa = sa + i0, *pb = sb + (j0 + WO - 1);
 #pragma unroll
-    for (int k = 0; k < VT; ++k) {
-        const int e = lane + 32 * k;
-        if (e < naw) {
-            v[k] = sa[i0 + e];
-            x[k] = (uint32_t)(i0 + e);
-        } else if (e >= WO - nbw) {
-            const int bi = j0 + (WO - 1 - e);
-            v[k] = sb[bi];
-            x[k] = (uint32_t)(na + bi);
-        } else {
-            v[k] = max_code<K>();
-            x[k] = 0xffffffffu;
+        for (int k = 0; k < VT; ++k) {
+            const int e = lane + 32 * k;
+            const bool in_a = e < naw;
+            v[k] = *(in_a ? pa + e : pb - e);
+            x[k] = in_a ? (uint32_t)(i0 + e) : (uint32_t)(na + j0 + WO - 1 - e);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VT; ++k) {
+            const int e = lane + 32 * k;
+            if (e < naw) {
+                v[k] = sa[i0 + e];
+                x[k] = (uint32_t)(i0 + e);
+            } else if (e >= WO - nbw) {
+                const int bi = j0 + (WO - 1 - e);
+                v[k] = sb[bi];
+                x[k] = (uint32_t)(na + bi);
+            } else {
+                v[k] = max_code<K>();
+                x[k] = 0xffffffffu;
+            }
         }
     }
     if constexpr (!HV) mbar_arrive(empty_bar);  // every shared read of this stage is done
-    // bitonic merger: register strides WO/2 .. 32, then lane strides 16 .. 1
+    // strides WO/2 .. 32: registers k and k + r of the same lane
 #pragma unroll
     for (int r = VT >> 1; r > 0; r >>= 1) {
 #pragma unroll
@@ -1064,36 +1156,97 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
             }
         }
     }
-#pragma unroll
-    for (int ls = 16; ls > 0; ls >>= 1) {
-        const bool up = lane & ls;
-#pragma unroll
-        for (int k = 0; k < VT; ++k) {
-            const K pk = shfl_xor_k<VT>(v[k], ls);
-            if constexpr (HV) {
-                const uint32_t px = __shfl_xor_sync(0xffffffffu, x[k], ls);
-                const bool take = up ? ki_less(v[k], x[k], pk, px) : ki_less(pk, px, v[k], x[k]);
-                v[k] = take ? pk : v[k];
-                x[k] = take ? px : x[k];
-            } else {
-                v[k] = up ? (v[k] < pk ? pk : v[k]) : (v[k] < pk ? v[k] : pk);
-            }
-        }
-    }
-    V vals[VT];
-    if constexpr (HV) {
-#pragma unroll
-        for (int k = 0; k < VT; ++k)
-            if (lane + 32 * k < d1 - d0) vals[k] = (int)x[k] < na ? sav[x[k]] : sbv[x[k] - na];
-        mbar_arrive(empty_bar);
-    }
-    K *out = dk + o_lo + d0;
+    // transpose 1: element e = lane + 32k -> lane e / VT, register e % VT
 #pragma unroll
     for (int k = 0; k < VT; ++k) {
         const int e = lane + 32 * k;
-        if (e < d1 - d0) {
-            out[e] = fin ? dec_code(v[k], codec) : v[k];
-            if constexpr (HV) dv[o_lo + d0 + e] = vals[k];
+        const int at = swz_chunk(e / E) * E + e % E;
+        wk[at] = v[k];
+        if constexpr (HV) wx[at] = x[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        const int at = swz_chunk(C * lane + r) * E;
+        ld_chunk<K, E>(wk + at, v + r * E);
+        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + r * E);
+    }
+    __syncwarp();
+    // now lane l holds elements VT*l + q; strides 16 .. VT cross lanes
+#pragma unroll
+    for (int s = 16; s >= VT; s >>= 1) {
+        const int ls = s / VT;
+        const bool up = lane & ls;
+#pragma unroll
+        for (int q = 0; q < VT; ++q) {
+            const K pk = shfl_xor_k<VT>(v[q], ls);
+            if constexpr (HV) {
+                const uint32_t px = __shfl_xor_sync(0xffffffffu, x[q], ls);
+                const bool take = up ? ki_less(v[q], x[q], pk, px) : ki_less(pk, px, v[q], x[q]);
+                v[q] = take ? pk : v[q];
+                x[q] = take ? px : x[q];
+            } else {
+                v[q] = up ? (v[q] < pk ? pk : v[q]) : (v[q] < pk ? v[q] : pk);
+            }
+        }
+    }
+    // strides below VT (and below 32): registers q and q + r
+#pragma unroll
+    for (int r = (VT < 32 ? VT : 32) >> 1; r > 0; r >>= 1) {
+#pragma unroll
+        for (int q = 0; q < VT; ++q) {
+            if ((q & r) == 0) {
+                if constexpr (HV) cas_pairs(v[q], x[q], v[q + r], x[q + r]);
+                else cas_keys(v[q], v[q + r]);
+            }
+        }
+    }
+    // transpose 2: lane l takes chunks l, l + 32, .. (element (32m + l)*E + p
+    // in register m*E + p)
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        const int at = swz_chunk(C * lane + r) * E;
+        st_chunk<K, E>(wk + at, v + r * E);
+        if constexpr (HV) st_chunk<uint32_t, E>(wx + at, x + r * E);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int at = swz_chunk(32 * m + lane) * E;
+        ld_chunk<K, E>(wk + at, v + m * E);
+        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + m * E);
+    }
+    __syncwarp();  // the scratch is free for the warp's next tile
+    const int cnt = d1 - d0;
+    V vals[VT];
+    if constexpr (HV) {
+#pragma unroll
+        for (int m = 0; m < C; ++m)
+#pragma unroll
+            for (int p = 0; p < E; ++p) {
+                const int i = m * E + p;
+                if ((32 * m + lane) * E + p < cnt) vals[i] = (int)x[i] < na ? sav[x[i]] : sbv[x[i] - na];
+            }
+        mbar_arrive(empty_bar);
+    }
+#pragma unroll
+    for (int i = 0; i < VT; ++i) v[i] = fin ? dec_code(v[i], codec) : v[i];
+    const int64_t o = o_lo + d0;
+    const bool aligned = (o % E) == 0;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int eb = (32 * m + lane) * E;  // first element of this chunk
+        if (aligned && eb + E <= cnt) {
+            st_chunk<K, E>(dk + o + eb, v + m * E);
+        } else {
+#pragma unroll
+            for (int p = 0; p < E; ++p)
+                if (eb + p < cnt) dk[o + eb + p] = v[m * E + p];
+        }
+        if constexpr (HV) {
+#pragma unroll
+            for (int p = 0; p < E; ++p)
+                if (eb + p < cnt) dv[o + eb + p] = vals[m * E + p];
         }
     }
 }
@@ -1107,26 +1260,34 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
 // does a candidate merge of VT outputs, stored as 16-byte vectors.  All waits
 // are bounded; a timeout records BS_ERR_TIMEOUT and ends the CTA.  Needs
 // 16-byte aligned buffers.
+// CTAs per SM the merge pipeline is compiled for (a register cap): as many
+// as its shared memory lets reside (228 KB per SM, 1 KB reserved per CTA),
+// but no more than leave each thread 56 registers (32-bit keys alone, warp
+// consumer) or 64 (otherwise).  Its speed follows the resident warps.
+template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE> constexpr int merge_min_ctas() {
+    const int by_smem = (int)((228 * 1024) / (tma_smem_bytes<K, V, THREADS, VT, STAGES, WARPMERGE>() + 1024));
+    const int regs = (WARPMERGE && sizeof(K) == 4 && !HasVal<V>::value) ? 56 : 64;
+    const int by_regs = 65536 / ((THREADS + 32) * regs);
+    const int m = by_smem < by_regs ? by_smem : by_regs;
+    return m < 1 ? 1 : m;
+}
+
 template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE>
-__global__ void __launch_bounds__(THREADS + 32)
+__global__ void __launch_bounds__(THREADS + 32, (merge_min_ctas<K, V, THREADS, VT, STAGES, WARPMERGE>()))
 merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
                  const int64_t *__restrict__ split, const int64_t *__restrict__ ntiles_total) {
     constexpr int TT = THREADS * VT;
     constexpr bool HV = HasVal<V>::value;
     using LY = TmaLayout<K, V, TT>;
+    using WS = WarpScratch<K, V, VT>;
+    constexpr size_t SCRATCH = WARPMERGE ? (THREADS / 32) * WS::bytes : 0;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage + SCRATCH);
     uint64_t *empty = full + STAGES;
-    auto stage_a = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
-    auto stage_b = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage + LY::keys); };
-    auto stage_av = [&](int s) {
-        return reinterpret_cast<V *>(smem_raw + s * LY::stage + 2 * LY::keys);
-    };
-    auto stage_bv = [&](int s) {
-        return reinterpret_cast<V *>(smem_raw + s * LY::stage + 2 * LY::keys + LY::vals);
-    };
+    auto stage_k = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
+    auto stage_v = [&](int s) { return reinterpret_cast<V *>(smem_raw + s * LY::stage + LY::keys); };
     auto stage_desc = [&](int s) {
-        return reinterpret_cast<StageDesc *>(smem_raw + s * LY::stage + 2 * LY::keys + 2 * LY::vals);
+        return reinterpret_cast<StageDesc *>(smem_raw + s * LY::stage + LY::keys + LY::vals);
     };
 
     if (threadIdx.x == 0) {
@@ -1149,6 +1310,8 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
         // claim a free stage and issue that tile's copies.
         const int lane = threadIdx.x - THREADS;
         int64_t it = 0;
+        int stg = 0;          // it % STAGES
+        uint32_t ph = 0;      // (it / STAGES) & 1
         for (int64_t base = blockIdx.x; base < total; base += 32 * (int64_t)gridDim.x) {
             const int64_t t = base + (int64_t)lane * gridDim.x;
             TilePair p{};
@@ -1159,11 +1322,11 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             }
             const int64_t left = (total - base + gridDim.x - 1) / gridDim.x;
             const int cnt = left < 32 ? (int)left : 32;
-            for (int j = 0; j < cnt; ++j, ++it) {
+            for (int j = 0; j < cnt; ++j, ++it, ph ^= (stg == STAGES - 1), stg = (stg == STAGES - 1) ? 0 : stg + 1) {
                 bool ok = true;
                 if (lane == j) {
-                    const int s = (int)(it % STAGES);
-                    if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), WAIT_LIMIT)) {
+                    const int s = stg;
+                    if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT)) {
                         if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
                         // drain: wait (bounded) for this CTA's copies still in flight
                         for (int64_t jt = (it > STAGES ? it - STAGES : 0); jt < it; ++jt)
@@ -1186,12 +1349,14 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
                             // below: the transaction count may go negative within a
                             // phase), then the plain writes, then the releasing
                             // arrive that publishes them
-                            d.a_off = stage_window(stage_a(s), src, n, q.a_lo, q.a_hi, &full[s], &issued);
-                            d.b_off = stage_window(stage_b(s), src, n, q.b_lo, q.b_hi, &full[s], &issued);
+                            const int ak = window_span<K>(q.a_lo, q.a_hi);
+                            d.a_off = stage_window(stage_k(s), src, n, q.a_lo, q.a_hi, &full[s], &issued);
+                            d.b_off = ak + stage_window(stage_k(s) + ak, src, n, q.b_lo, q.b_hi, &full[s], &issued);
                             if constexpr (HV) {
                                 const V *srcv = p.src ? buf_v1 : buf_v0;
-                                d.av_off = stage_window(stage_av(s), srcv, n, q.a_lo, q.a_hi, &full[s], &issued);
-                                d.bv_off = stage_window(stage_bv(s), srcv, n, q.b_lo, q.b_hi, &full[s], &issued);
+                                const int av = window_span<V>(q.a_lo, q.a_hi);
+                                d.av_off = stage_window(stage_v(s), srcv, n, q.a_lo, q.a_hi, &full[s], &issued);
+                                d.bv_off = av + stage_window(stage_v(s) + av, srcv, n, q.b_lo, q.b_hi, &full[s], &issued);
                             }
                         }
                         *stage_desc(s) = d;
@@ -1206,22 +1371,26 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
 
     // ---------------- consumers
     const int tid = threadIdx.x;
-    int64_t it = 0;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-        const int s = (int)(it % STAGES);
-        if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), WAIT_LIMIT)) {
+    int stg = 0;      // tile number % STAGES
+    uint32_t ph = 0;  // (tile number / STAGES) & 1
+    for (int64_t t = blockIdx.x; t < total;
+         t += gridDim.x, ph ^= (stg == STAGES - 1), stg = (stg == STAGES - 1) ? 0 : stg + 1) {
+        const int s = stg;
+        if (!mbar_wait(&full[s], ph, WAIT_LIMIT)) {
             if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
             return;
         }
         const StageDesc d = *stage_desc(s);
         if (d.flags & 1) {
-            const K *sa = stage_a(s) + d.a_off;
-            const K *sb = stage_b(s) + d.b_off;
+            const K *sa = stage_k(s) + d.a_off;
+            const K *sb = stage_k(s) + d.b_off;
             const int na = d.na, nb = d.nb, total_out = na + nb;
             if constexpr (WARPMERGE) {
-                warp_merge_tile<K, V, VT>(sa, sb, stage_av(s) + d.av_off, stage_bv(s) + d.bv_off, na, nb,
+                unsigned char *ws = smem_raw + STAGES * LY::stage + (tid >> 5) * WS::bytes;
+                warp_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb,
                                           (d.flags & 2) ? buf_k1 : buf_k0, (d.flags & 2) ? buf_v1 : buf_v0,
-                                          d.o_lo, (d.flags & 4) != 0, codec, &empty[s], tid);
+                                          d.o_lo, (d.flags & 4) != 0, codec, &empty[s], tid,
+                                          reinterpret_cast<K *>(ws), reinterpret_cast<uint32_t *>(ws + WS::keys));
                 if (tid == 0)
                     atomicAdd(g.counters + CLS_MERGE,
                               2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
@@ -1255,8 +1424,8 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             V v[VT];
             if constexpr (HV) {
                 bitonic_merge_pairs<VT>(k, idx);
-                const V *sav = stage_av(s) + d.av_off;
-                const V *sbv = stage_bv(s) + d.bv_off;
+                const V *sav = stage_v(s) + d.av_off;
+                const V *sbv = stage_v(s) + d.bv_off;
 #pragma unroll
                 for (int u = 0; u < VT; ++u)
                     if (u < count) v[u] = (int)idx[u] < na ? sav[idx[u]] : sbv[idx[u] - na];

@@ -18,7 +18,13 @@ template <class Kern> static int resident_ctas(Kern kern, int threads, size_t sm
     return nb;
 }
 
+// Lets `kern` use `smem` bytes of dynamic shared memory and asks for the
+// largest shared-memory carveout, so that as many CTAs are resident as the
+// occupancy calculator (which the persistent grids are sized by) assumes.
 template <class Kern> static bool allow_smem(Kern kern, size_t smem) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        cudaGetLastError();  // a hint only
     if (smem <= 48 * 1024) return true;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
            cudaSuccess;
@@ -41,13 +47,13 @@ bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles)
     constexpr int STAGES = 2;
     constexpr int TM = MT * MVT;
     constexpr size_t smem = smem_bytes<K, V>(TM);
-    constexpr size_t msmem = tma_smem_bytes<K, V, MT, MVT, STAGES>();
     auto mk = merge_kernel<K, V, MT, MVT>;
-    auto mt = a.merge_consumer == 1 ? merge_tma_kernel<K, V, MT, MVT, STAGES, false>
-                                    : merge_tma_kernel<K, V, MT, MVT, STAGES, true>;
+    const int ci = a.merge_consumer == 1 ? 1 : 0;
+    auto mt = ci ? merge_tma_kernel<K, V, MT, MVT, STAGES, false> : merge_tma_kernel<K, V, MT, MVT, STAGES, true>;
+    const size_t msmem = ci ? tma_smem_bytes<K, V, MT, MVT, STAGES, false>()
+                            : tma_smem_bytes<K, V, MT, MVT, STAGES, true>();
     auto pk = partition_kernel<K>;
     static std::atomic<int> occ_mk{0}, occ_mt[2] = {{0}, {0}};
-    const int ci = a.merge_consumer == 1 ? 1 : 0;
     if (!occ_mk.load()) {
         if (!allow_smem(mk, smem)) return false;
         occ_mk.store(resident_ctas(mk, MT, smem));
