@@ -45,11 +45,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["keys", "batched", "serving", "memory", "psweep",
+    ap.add_argument("--workload", choices=["keys", "pairs", "batched", "serving", "memory", "psweep",
                                            "localsort"],
                     default="keys",
-                    help="keys: one 2^log2n int32 array (the headline); batched: many "
+                    help="keys: one 2^log2n int32 array (the headline); pairs: 2^pairs-log2n "
+                         "uint64 keys with int32 index payloads (stable); batched: many "
                          "arrays of log-uniform length in one graph-captured segmented sort")
+    ap.add_argument("--pairs-log2n", type=int, default=27)
+    ap.add_argument("--pairs-dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--seg-lo", type=int, default=16)
     ap.add_argument("--seg-hi-log2", type=int, default=17)
@@ -192,7 +195,7 @@ def config(args):
             "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
             "merge_kernel": args.merge, "merge_vt": args.merge_vt or 16,
             "merge_tile_keys": 1 << (args.merge_tile_log2 or args.tile_log2),
-            "merge_consumer": ["warp", "thread"][args.merge_consumer],
+            "merge_consumer": ["thread sequential merge", "warp bitonic"][args.merge_consumer],
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
             "stream": "torch current stream", "out_of_place": True}
 
@@ -396,6 +399,99 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- stable pairs workload
+
+def run_pairs(args):
+    """2^27 uint64 keys (uniform, or Zipf(1.1) over 2^20 distinct keys) with an
+    int32 payload = original index, p = 2, sorted stably through bs_sort_pairs.
+    12 bytes move per item per pass."""
+    import numpy as np
+    import torch
+
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300 import workloads as W
+
+    n = 1 << args.pairs_log2n
+    keys_h = (W.uniform_uint64(n, seed=SEED) if args.pairs_dist == "uniform"
+              else W.zipf_uint64(n, seed=SEED))
+    vals_h = W.index_payload(n)
+    sorter = abi.Sorter(0, tile_log2=args.tile_log2, merge_kernel=args.merge, merge_vt=args.merge_vt,
+                        merge_tile_log2=args.merge_tile_log2, merge_consumer=args.merge_consumer)
+    dk, dv = torch.from_numpy(keys_h).cuda(), torch.from_numpy(vals_h).cuda()
+    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        abi.bs_sort_pairs(sorter.h, dk.data_ptr(), ko.data_ptr(), dv.data_ptr(), vo.data_ptr(), n,
+                          "uint64", "int32", args.p, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    sorter.sync()
+    # the output is the stable sort iff: the payload is a permutation, every key
+    # travelled with its payload, keys are nondecreasing, equal keys keep order
+    idx = vo.long()
+    assert bool((torch.bincount(idx, minlength=n) == 1).all()), "payload not a permutation"
+    assert torch.equal(ko.view(torch.int64), dk.view(torch.int64)[idx]), "key and payload parted"
+    code = ko.view(torch.int64) ^ torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    assert bool((code[1:] >= code[:-1]).all()), "keys not sorted"
+    eq = code[1:] == code[:-1]
+    assert bool((vo[1:][eq] > vo[:-1][eq]).all()), "not stable"
+    del idx, code, eq
+
+    abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+    counts, _ = abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
+    kb = min(args.steps, 10)
+    abi.bs_launch_stats(sorter.h, reset=True)
+    sorter.set_timing(True)
+    for _ in range(kb):
+        step()
+    torch.cuda.synchronize()
+    sorter.set_timing(False)
+    kms, kn = sorter.kernel_times()
+    _, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
+    peak, peak_src = load_peak()
+    kernels = {}
+    for cls in ("tile_sort", "merge", "partition", "setup"):
+        if kn[cls]:
+            avg = kms[cls] / kn[cls]
+            per = kbytes[cls] / kn[cls]
+            kernels[cls] = {"launches_per_step": kn[cls] / kb, "ms_per_launch": avg, "bytes_per_launch": per,
+                            "gbs": per / (avg * 1e-3) / 1e9 if per else None}
+    dom = max(("tile_sort", "merge"), key=lambda c: kms[c])
+    passes = kernels["tile_sort"]["launches_per_step"] + kernels["merge"]["launches_per_step"]
+    line = {
+        "metric": "Gkeys/s and % HBM roofline, stable uint64+int32 pairs on 1 GB300", "value": n / (ms * 1e-3) / 1e9,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+i32", "data": "synthetic",
+        "config": {"workload": f"stable pair sort, 2^{args.pairs_log2n} {args.pairs_dist} uint64 keys + int32 "
+                               f"index payload, p={args.p} blocks", "n": n, "p": args.p,
+                   "dist": args.pairs_dist, "tile_keys": 1 << args.tile_log2, "seed": SEED,
+                   "l2": "inputs (12 B x n = 1.5 GiB at 2^27) larger than the 129 MB L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": kernels[dom]["gbs"] / peak, "traffic": None,
+                     "kernel": "merge pass" if dom == "merge" else "tile sort",
+                     "peak_source": f"{peak_src} (copy bandwidth)", "passes_per_step": passes,
+                     "end_to_end_frac": passes * 2 * 12 * n / (ms * 1e-3) / 1e9 / peak},
+        "gpu_launches": int(sum(counts.values())), "clocks": clk, "kernels": kernels,
+        "checked": "payload permutation, keys carried with payloads, nondecreasing, stable",
+    }
+    sorter.close()
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -685,6 +781,8 @@ def main():
         return run_psweep(args)
     if args.workload == "localsort":
         return run_localsort(args)
+    if args.workload == "pairs":
+        return run_pairs(args)
     return run_ours(args)
 
 

@@ -256,9 +256,10 @@ typedef enum {
     BS_OPT_MERGE_TILE_LOG2 = 7,/* merge-pass tile 2^value keys: 0 (default) = the sort tile,
                                 or 11 .. the sort tile's log2; smaller merge tiles use less
                                 shared memory, so more CTAs fit per SM */
-    BS_OPT_MERGE_CONSUMER = 8 /* TMA merge consumers: 0 (default) each warp merges a slice with
-                                a bitonic merger over registers and shuffles; 1 each thread
-                                finds its own merge-path split and merges VT candidates */
+    BS_OPT_MERGE_CONSUMER = 8 /* TMA merge consumers: 0 (default) each thread finds its own
+                                merge-path split and merges its VT outputs sequentially;
+                                1 each warp merges a slice with a bitonic merger over
+                                registers, shuffles and a shared-memory transpose */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

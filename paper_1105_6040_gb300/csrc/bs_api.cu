@@ -169,7 +169,7 @@ struct bs_handle {
     int schedule = BS_SCHEDULE_TREE;
     int local_sort = BS_LOCAL_MERGE;
     int merge_tile_log2 = 0;  // 0: the sort tile
-    int merge_consumer = 0;   // 0 warp bitonic merger, 1 per-thread candidate merge
+    int merge_consumer = 0;   // 0 per-thread sequential merge, 1 warp bitonic merger
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;

@@ -1008,11 +1008,13 @@ struct StageDesc {
 
 // One stage holds the tile's A and B windows back to back (B's starts at the
 // next 16-byte boundary after A's), so it needs the tile's size plus the
-// rounding of four window ends: TT + 6 * (16 / item size) items.
+// rounding of four window ends: TT + 6 * (16 / item size) items; the key
+// window has 32 more, which a thread consumer's run-ahead reads past the end
+// of B may touch (their values are never used).
 template <class K, class V, int TT> struct TmaLayout {
     static constexpr int EK = 16 / (int)sizeof(K);
     static constexpr int EV = sizeof(V) > 1 ? 16 / (int)sizeof(V) : 1;
-    static constexpr size_t keys = ((size_t)(TT + 6 * EK) * sizeof(K) + 127) & ~size_t(127);
+    static constexpr size_t keys = ((size_t)(TT + 6 * EK + 32) * sizeof(K) + 127) & ~size_t(127);
     static constexpr size_t vals =
         sizeof(V) > 1 ? (((size_t)(TT + 6 * EV) * sizeof(V) + 127) & ~size_t(127)) : 0;
     static constexpr size_t stage = keys + vals + 128;  // windows + descriptor
@@ -1056,25 +1058,112 @@ template <class T, int N> __device__ __forceinline__ void st_chunk(T *p, const T
 
 template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-    return STAGES * TmaLayout<K, V, THREADS * VT>::stage +
-           (WARPMERGE ? (THREADS / 32) * WarpScratch<K, V, VT>::bytes : 0) + 2 * STAGES * sizeof(uint64_t) +
-           128;
+    return STAGES * TmaLayout<K, V, THREADS * VT>::stage + (THREADS / 32) * WarpScratch<K, V, VT>::bytes +
+           2 * STAGES * sizeof(uint64_t) + 128;
 }
 
-// Warp consumer of one staged tile: warp w produces outputs [d0, d1) of the
-// tile (32*VT of them).  The warp finds the merge-path splits at d0 and d1
-// (a 17-way search per half-warp), then reads its A slice followed by its B
-// slice reversed -- a bitonic sequence, padded in the middle with the
-// largest key -- striped across lanes (element e at lane e%32, register
-// e/32: conflict-free shared loads) and sorts it with a bitonic merger: the
-// strides of 32 and more are register compare-exchanges in this layout; a
-// transpose through the warp's scratch then gives each lane VT consecutive
-// elements, so that of the strides below 32 only those of VT and more cross
-// lanes (shuffles) and the rest are register compare-exchanges again.  A
-// second transpose hands lane l the 16-byte chunks l, l+32, .. of the warp's
-// output, so that every store instruction writes 512 contiguous bytes.
-// Pairs compare (key, staging index), carry the index through both
-// transposes and fetch their values at the end.
+// The merge-path splits of a tile at the warp's output range [d0, d1):
+// lanes 0-15 search diagonal d0, lanes 16-31 diagonal d1.  Each half-warp
+// tests 16 evenly spaced points of the interval holding its split (the
+// predicate B[d-1-i] < A[i] is false then true) and keeps the piece between
+// the last false and the first true test: a 17-way search, 3 rounds for a
+// 4096-key tile.  Returns the A index of both splits in every lane.
+template <class K>
+__device__ __forceinline__ void warp_splits(const K *sa, const K *sb, int na, int nb, int d0, int d1, int lane,
+                                            int &i0, int &i1) {
+    const int half = lane >> 4, sub = lane & 15;
+    const int dd = half ? d1 : d0;
+    int lo = dd > nb ? dd - nb : 0, hi = dd < na ? dd : na;
+    while (__any_sync(0xffffffffu, lo < hi)) {
+        const bool live = lo < hi;
+        const int mid = lo + ((sub + 1) * (hi - lo)) / 17;  // lo <= mid < hi
+        const bool test = live && sb[dd - 1 - mid] < sa[mid];
+        const unsigned yes = (__ballot_sync(0xffffffffu, test) >> (16 * half)) & 0xffffu;
+        const int f = yes ? __ffs(yes) - 1 : 16;  // first point whose test holds
+        const int mprev = __shfl_sync(0xffffffffu, mid, 16 * half + (f > 0 ? f - 1 : 0));
+        const int mf = __shfl_sync(0xffffffffu, mid, 16 * half + (f < 16 ? f : 15));
+        if (live) {
+            if (f > 0) lo = mprev + 1;
+            if (f < 16) hi = mf;
+        }
+    }
+    i0 = __shfl_sync(0xffffffffu, lo, 0);
+    i1 = __shfl_sync(0xffffffffu, lo, 16);
+}
+
+// Stores a warp's 32*VT merged outputs, held lane-blocked (lane l has
+// outputs VT*l .. VT*l + VT - 1; for pairs x[] holds their staging indices,
+// A's first, then B's from na).  A transpose through the warp's scratch
+// hands lane l the 16-byte chunks l, l+32, .. so that every store
+// instruction writes 512 contiguous bytes; pairs fetch their values from the
+// stage by index and then release it (keys-only callers release it before).
+// cnt = valid outputs, o = global index of the first.
+template <class K, class V, int VT>
+__device__ __forceinline__ void store_warp_outputs(K (&v)[VT], uint32_t (&x)[VT], const V *sav, const V *sbv,
+                                                   int na, K *dk, V *dv, int64_t o, int cnt, bool fin, int codec,
+                                                   uint64_t *empty_bar, int lane, K *wk, uint32_t *wx) {
+    constexpr bool HV = HasVal<V>::value;
+    constexpr int E = 16 / (int)sizeof(K);  // keys per 16-byte chunk
+    constexpr int C = VT / E;               // chunks per lane
+    static_assert(C >= 1 && VT % E == 0, "whole chunks per lane");
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        const int at = swz_chunk(C * lane + r) * E;
+        st_chunk<K, E>(wk + at, v + r * E);
+        if constexpr (HV) st_chunk<uint32_t, E>(wx + at, x + r * E);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int at = swz_chunk(32 * m + lane) * E;
+        ld_chunk<K, E>(wk + at, v + m * E);
+        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + m * E);
+    }
+    __syncwarp();  // the scratch is free for the warp's next tile
+    V vals[VT];
+    if constexpr (HV) {
+#pragma unroll
+        for (int m = 0; m < C; ++m)
+#pragma unroll
+            for (int p = 0; p < E; ++p) {
+                const int i = m * E + p;
+                if ((32 * m + lane) * E + p < cnt) vals[i] = (int)x[i] < na ? sav[x[i]] : sbv[x[i] - na];
+            }
+        mbar_arrive(empty_bar);
+    }
+    if (fin) {
+#pragma unroll
+        for (int i = 0; i < VT; ++i) v[i] = dec_code(v[i], codec);
+    }
+    const bool aligned = (o % E) == 0;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int eb = (32 * m + lane) * E;  // first output of this chunk
+        if (aligned && eb + E <= cnt) {
+            st_chunk<K, E>(dk + o + eb, v + m * E);
+        } else {
+#pragma unroll
+            for (int p = 0; p < E; ++p)
+                if (eb + p < cnt) dk[o + eb + p] = v[m * E + p];
+        }
+        if constexpr (HV) {
+#pragma unroll
+            for (int p = 0; p < E; ++p)
+                if (eb + p < cnt) dv[o + eb + p] = vals[m * E + p];
+        }
+    }
+}
+
+// Warp consumer of one staged tile (bitonic): warp w produces outputs
+// [d0, d1) of the tile (32*VT of them).  After its two merge-path splits it
+// reads its A slice followed by its B slice reversed -- a bitonic sequence,
+// padded in the middle with the largest key -- striped across lanes
+// (element e at lane e%32, register e/32: conflict-free shared loads) and
+// sorts it with a bitonic merger: the strides of 32 and more are register
+// compare-exchanges in this layout; a transpose through the warp's scratch
+// then gives each lane VT consecutive elements, so that of the strides
+// below 32 only those of VT and more cross lanes (shuffles) and the rest are
+// register compare-exchanges again.  Pairs compare (key, staging index).
 template <class K, class V, int VT>
 __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const V *sav, const V *sbv,
                                                 int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
@@ -1082,38 +1171,13 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
                                                 uint32_t *wx) {
     constexpr bool HV = HasVal<V>::value;
     constexpr int WO = 32 * VT;
-    constexpr int E = 16 / (int)sizeof(K);  // keys per 16-byte chunk
-    constexpr int C = VT / E;               // chunks per lane
-    static_assert(C >= 1 && VT % E == 0, "whole chunks per lane");
+    constexpr int E = 16 / (int)sizeof(K);
+    constexpr int C = VT / E;
     const int lane = tid & 31, w = tid >> 5;
     const int total = na + nb;
     const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
-    // the merge-path splits at d0 (lanes 0-15) and d1 (lanes 16-31): each
-    // half-warp tests 16 evenly spaced points of the interval holding its
-    // split, whose predicate B[d-1-i] < A[i] is false then true, and keeps
-    // the piece between the last false and the first true test (17-way
-    // search: 3 rounds for a 4096-key tile)
     int i0, i1;
-    {
-        const int half = lane >> 4, sub = lane & 15;
-        const int dd = half ? d1 : d0;
-        int lo = dd > nb ? dd - nb : 0, hi = dd < na ? dd : na;
-        while (__any_sync(0xffffffffu, lo < hi)) {
-            const bool live = lo < hi;
-            const int mid = lo + ((sub + 1) * (hi - lo)) / 17;  // lo <= mid < hi
-            const bool test = live && sb[dd - 1 - mid] < sa[mid];
-            const unsigned yes = (__ballot_sync(0xffffffffu, test) >> (16 * half)) & 0xffffu;
-            const int f = yes ? __ffs(yes) - 1 : 16;  // first point whose test holds
-            const int mprev = __shfl_sync(0xffffffffu, mid, 16 * half + (f > 0 ? f - 1 : 0));
-            const int mf = __shfl_sync(0xffffffffu, mid, 16 * half + (f < 16 ? f : 15));
-            if (live) {
-                if (f > 0) lo = mprev + 1;
-                if (f < 16) hi = mf;
-            }
-        }
-        i0 = __shfl_sync(0xffffffffu, lo, 0);
-        i1 = __shfl_sync(0xffffffffu, lo, 16);
-    }
+    warp_splits<K>(sa, sb, na, nb, d0, d1, lane, i0, i1);
     const int naw = i1 - i0, j0 = d0 - i0, nbw = (d1 - d0) - naw;
     K v[VT];
     uint32_t x[VT];
@@ -1156,7 +1220,7 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
             }
         }
     }
-    // transpose 1: element e = lane + 32k -> lane e / VT, register e % VT
+    // transpose: element e = lane + 32k -> lane e / VT, register e % VT
 #pragma unroll
     for (int k = 0; k < VT; ++k) {
         const int e = lane + 32 * k;
@@ -1201,72 +1265,74 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
             }
         }
     }
-    // transpose 2: lane l takes chunks l, l + 32, .. (element (32m + l)*E + p
-    // in register m*E + p)
-#pragma unroll
-    for (int r = 0; r < C; ++r) {
-        const int at = swz_chunk(C * lane + r) * E;
-        st_chunk<K, E>(wk + at, v + r * E);
-        if constexpr (HV) st_chunk<uint32_t, E>(wx + at, x + r * E);
+    store_warp_outputs<K, V, VT>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec, empty_bar, lane, wk,
+                                 wx);
+}
+
+// Thread consumer of one staged tile (serial merge): lane l of warp w
+// produces outputs [d, d + VT) of the tile, d = 32*VT*w + VT*l.  Its
+// merge-path split is found by a binary search inside the warp's split
+// range; then VT steps of the sequential merge each take the smaller head
+// (A's on a tie, which is the stable order, so pairs need no index
+// compares) and load the next item of that run: one shared load and a few
+// integer ops per output.
+template <class K, class V, int VT>
+__device__ __forceinline__ void thread_merge_tile(const K *sa, const K *sb, const V *sav, const V *sbv,
+                                                  int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
+                                                  int codec, uint64_t *empty_bar, int tid, K *wk,
+                                                  uint32_t *wx) {
+    constexpr bool HV = HasVal<V>::value;
+    constexpr int WO = 32 * VT;
+    const int lane = tid & 31, w = tid >> 5;
+    const int total = na + nb;
+    const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
+    int i0, i1;
+    warp_splits<K>(sa, sb, na, nb, d0, d1, lane, i0, i1);
+    const int j0 = d0 - i0, j1 = d1 - i1;
+    const int diag = min(d0 + lane * VT, d1);
+    // this lane's split lies in [i0, i1] with diag - i in [j0, j1]
+    int lo = max(i0, diag - j1), hi = min(i1, diag - j0);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sb[diag - 1 - mid] < sa[mid]) hi = mid;
+        else lo = mid + 1;
     }
-    __syncwarp();
+    int i = lo;
+    K a = sa[i], b = sb[diag - i];  // past a run's end these are not used
+    K v[VT];
+    uint32_t x[VT];
 #pragma unroll
-    for (int m = 0; m < C; ++m) {
-        const int at = swz_chunk(32 * m + lane) * E;
-        ld_chunk<K, E>(wk + at, v + m * E);
-        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + m * E);
+    for (int u = 0; u < VT; ++u) {
+        const int j = diag + u - i;
+        const bool tb = i >= na || (j < nb && b < a);  // take B's head
+        v[u] = tb ? b : a;
+        if constexpr (HV) x[u] = tb ? (uint32_t)(na + j) : (uint32_t)i;
+        i += tb ? 0 : 1;
+        const K nxt = *(tb ? sb + (j + 1) : sa + i);
+        a = tb ? a : nxt;
+        b = tb ? nxt : b;
     }
-    __syncwarp();  // the scratch is free for the warp's next tile
-    const int cnt = d1 - d0;
-    V vals[VT];
-    if constexpr (HV) {
-#pragma unroll
-        for (int m = 0; m < C; ++m)
-#pragma unroll
-            for (int p = 0; p < E; ++p) {
-                const int i = m * E + p;
-                if ((32 * m + lane) * E + p < cnt) vals[i] = (int)x[i] < na ? sav[x[i]] : sbv[x[i] - na];
-            }
-        mbar_arrive(empty_bar);
-    }
-#pragma unroll
-    for (int i = 0; i < VT; ++i) v[i] = fin ? dec_code(v[i], codec) : v[i];
-    const int64_t o = o_lo + d0;
-    const bool aligned = (o % E) == 0;
-#pragma unroll
-    for (int m = 0; m < C; ++m) {
-        const int eb = (32 * m + lane) * E;  // first element of this chunk
-        if (aligned && eb + E <= cnt) {
-            st_chunk<K, E>(dk + o + eb, v + m * E);
-        } else {
-#pragma unroll
-            for (int p = 0; p < E; ++p)
-                if (eb + p < cnt) dk[o + eb + p] = v[m * E + p];
-        }
-        if constexpr (HV) {
-#pragma unroll
-            for (int p = 0; p < E; ++p)
-                if (eb + p < cnt) dv[o + eb + p] = vals[m * E + p];
-        }
-    }
+    if constexpr (!HV) mbar_arrive(empty_bar);  // every shared read of this stage is done
+    store_warp_outputs<K, V, VT>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec, empty_bar, lane, wk,
+                                 wx);
 }
 
 // Merge pass with a TMA pipeline (warp specialised, persistent).  The last
 // warp produces: its lanes compute the A and B slices of 32 of this CTA's
 // tiles at a time and stage them by 1-D bulk copies into a ring of STAGES
 // shared-memory stages (full/empty mbarriers).  THREADS consumer threads
-// take each stage: either every warp merges 32*VT outputs with the warp
-// bitonic merger (WARPMERGE), or every thread finds its merge-path split and
-// does a candidate merge of VT outputs, stored as 16-byte vectors.  All waits
-// are bounded; a timeout records BS_ERR_TIMEOUT and ends the CTA.  Needs
-// 16-byte aligned buffers.
+// take each stage; every warp produces 32*VT outputs, either with the warp
+// bitonic merger (WARPMERGE) or with one sequential merge of VT outputs per
+// thread, and stores them as 512-byte runs.  All waits are bounded; a
+// timeout records BS_ERR_TIMEOUT and ends the CTA.  Needs 16-byte aligned
+// buffers.
 // CTAs per SM the merge pipeline is compiled for (a register cap): as many
 // as its shared memory lets reside (228 KB per SM, 1 KB reserved per CTA),
-// but no more than leave each thread 56 registers (32-bit keys alone, warp
-// consumer) or 64 (otherwise).  Its speed follows the resident warps.
+// but no more than leave each thread 56 registers (32-bit keys alone) or 64
+// (otherwise).  Its speed follows the resident warps.
 template <class K, class V, int THREADS, int VT, int STAGES, bool WARPMERGE> constexpr int merge_min_ctas() {
     const int by_smem = (int)((228 * 1024) / (tma_smem_bytes<K, V, THREADS, VT, STAGES, WARPMERGE>() + 1024));
-    const int regs = (WARPMERGE && sizeof(K) == 4 && !HasVal<V>::value) ? 56 : 64;
+    const int regs = (sizeof(K) == 4 && !HasVal<V>::value) ? 56 : 64;
     const int by_regs = 65536 / ((THREADS + 32) * regs);
     const int m = by_smem < by_regs ? by_smem : by_regs;
     return m < 1 ? 1 : m;
@@ -1280,7 +1346,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
     constexpr bool HV = HasVal<V>::value;
     using LY = TmaLayout<K, V, TT>;
     using WS = WarpScratch<K, V, VT>;
-    constexpr size_t SCRATCH = WARPMERGE ? (THREADS / 32) * WS::bytes : 0;
+    constexpr size_t SCRATCH = (THREADS / 32) * WS::bytes;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STAGES * LY::stage + SCRATCH);
     uint64_t *empty = full + STAGES;
@@ -1385,82 +1451,18 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             const K *sa = stage_k(s) + d.a_off;
             const K *sb = stage_k(s) + d.b_off;
             const int na = d.na, nb = d.nb, total_out = na + nb;
-            if constexpr (WARPMERGE) {
-                unsigned char *ws = smem_raw + STAGES * LY::stage + (tid >> 5) * WS::bytes;
-                warp_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb,
-                                          (d.flags & 2) ? buf_k1 : buf_k0, (d.flags & 2) ? buf_v1 : buf_v0,
-                                          d.o_lo, (d.flags & 4) != 0, codec, &empty[s], tid,
-                                          reinterpret_cast<K *>(ws), reinterpret_cast<uint32_t *>(ws + WS::keys));
-                if (tid == 0)
-                    atomicAdd(g.counters + CLS_MERGE,
-                              2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
-                continue;
-            }
-            const int diag = min(tid * VT, total_out);
-            const int i = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
-            const int j = diag - i;
-            const int count = min(VT, total_out - diag);
-            K k[VT];
-            uint32_t idx[VT];
-            // candidate merge straight from the staged windows (A before B);
-            // no barrier among the consumers, so every wait stays bounded
-#pragma unroll
-            for (int u = 0; u < VT; ++u) {
-                const int ia = i + u, ib = j + VT - 1 - u;
-                if constexpr (HV) {
-                    K x = max_code<K>(), y = max_code<K>();
-                    uint32_t xi = 0xffffffffu, yi = 0xffffffffu;
-                    if (ia < na) x = sa[ia], xi = (uint32_t)ia;
-                    if (ib < nb) y = sb[ib], yi = (uint32_t)(na + ib);
-                    const bool tx = ki_less(x, xi, y, yi);
-                    k[u] = tx ? x : y;
-                    idx[u] = tx ? xi : yi;
-                } else {
-                    const K x = ia < na ? sa[ia] : max_code<K>();
-                    const K y = ib < nb ? sb[ib] : max_code<K>();
-                    k[u] = x < y ? x : y;
-                }
-            }
-            V v[VT];
-            if constexpr (HV) {
-                bitonic_merge_pairs<VT>(k, idx);
-                const V *sav = stage_v(s) + d.av_off;
-                const V *sbv = stage_v(s) + d.bv_off;
-#pragma unroll
-                for (int u = 0; u < VT; ++u)
-                    if (u < count) v[u] = (int)idx[u] < na ? sav[idx[u]] : sbv[idx[u] - na];
-            } else {
-                bitonic_merge_keys<VT>(k);
-            }
-            // all shared reads of this stage are done: hand it back
-            mbar_arrive(&empty[s]);
-            const bool fin = (d.flags & 4) != 0;
+            unsigned char *ws = smem_raw + STAGES * LY::stage + (tid >> 5) * WS::bytes;
             K *dk = (d.flags & 2) ? buf_k1 : buf_k0;
-            const int64_t o = d.o_lo + diag;
-#pragma unroll
-            for (int u = 0; u < VT; ++u) k[u] = fin ? dec_code(k[u], codec) : k[u];
-            constexpr int E = 16 / sizeof(K);
-            if (count == VT && (o % E) == 0) {
-#pragma unroll
-                for (int u = 0; u < VT; u += E) {
-                    if constexpr (sizeof(K) == 4)
-                        *reinterpret_cast<uint4 *>(dk + o + u) =
-                            make_uint4((uint32_t)k[u], (uint32_t)k[u + 1], (uint32_t)k[u + 2], (uint32_t)k[u + 3]);
-                    else
-                        *reinterpret_cast<ulonglong2 *>(dk + o + u) =
-                            make_ulonglong2((unsigned long long)k[u], (unsigned long long)k[u + 1]);
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < VT; ++u)
-                    if (u < count) dk[o + u] = k[u];
-            }
-            if constexpr (HV) {
-                V *dv = (d.flags & 2) ? buf_v1 : buf_v0;
-#pragma unroll
-                for (int u = 0; u < VT; ++u)
-                    if (u < count) dv[o + u] = v[u];
-            }
+            V *dv = (d.flags & 2) ? buf_v1 : buf_v0;
+            const bool fin = (d.flags & 4) != 0;
+            if constexpr (WARPMERGE)
+                warp_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv,
+                                          d.o_lo, fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),
+                                          reinterpret_cast<uint32_t *>(ws + WS::keys));
+            else
+                thread_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv,
+                                            d.o_lo, fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),
+                                            reinterpret_cast<uint32_t *>(ws + WS::keys));
             if (tid == 0)
                 atomicAdd(g.counters + CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
         } else {

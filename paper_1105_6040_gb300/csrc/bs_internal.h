@@ -37,7 +37,7 @@ struct PassArgs {
                               // instead of the cross-block tree (keys only, padded blocks)
     int local_sort;           // tile sort: 0 network + merges, 1 bubble (Fig. 2), 2 quick (Fig. 4)
     int merge_tile_log2;      // merge-pass tile (0: the sort tile; else 11 .. logT)
-    int merge_consumer;       // TMA merge consumers: 0 warp bitonic merger, 1 per-thread candidates
+    int merge_consumer;       // TMA merge consumers: 0 per-thread sequential merge, 1 warp bitonic
 };
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };

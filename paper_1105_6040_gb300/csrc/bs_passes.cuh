@@ -37,6 +37,7 @@ static inline int64_t grid_for(int64_t work, int64_t resident) {
 
 // Shared memory a CTA may use while still leaving room for a second CTA.
 constexpr size_t TMA_SMEM_AUTO_LIMIT = 112 * 1024;
+constexpr int MERGE_STAGES = 2;  // stages of the TMA merge pipeline
 constexpr size_t SMEM_OPT_IN_LIMIT = 227 * 1024;
 constexpr int PART_THREADS = 256;  // partition threads per CTA
 
@@ -44,14 +45,13 @@ constexpr int PART_THREADS = 256;  // partition threads per CTA
 // the TMA pipeline (when allowed and it fits) or the plain kernel.
 template <class K, class V, int MT, int MVT>
 bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
-    constexpr int STAGES = 2;
+    constexpr int STAGES = MERGE_STAGES;
     constexpr int TM = MT * MVT;
     constexpr size_t smem = smem_bytes<K, V>(TM);
     auto mk = merge_kernel<K, V, MT, MVT>;
-    const int ci = a.merge_consumer == 1 ? 1 : 0;
-    auto mt = ci ? merge_tma_kernel<K, V, MT, MVT, STAGES, false> : merge_tma_kernel<K, V, MT, MVT, STAGES, true>;
-    const size_t msmem = ci ? tma_smem_bytes<K, V, MT, MVT, STAGES, false>()
-                            : tma_smem_bytes<K, V, MT, MVT, STAGES, true>();
+    const int ci = a.merge_consumer == 1 ? 1 : 0;  // 1: warp bitonic consumers
+    auto mt = ci ? merge_tma_kernel<K, V, MT, MVT, STAGES, true> : merge_tma_kernel<K, V, MT, MVT, STAGES, false>;
+    const size_t msmem = tma_smem_bytes<K, V, MT, MVT, STAGES, true>();
     auto pk = partition_kernel<K>;
     static std::atomic<int> occ_mk{0}, occ_mt[2] = {{0}, {0}};
     if (!occ_mk.load()) {
@@ -87,6 +87,18 @@ bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles)
     return L.end(L.owner, CLS_MERGE, L.stream);
 }
 
+// Shared memory of the TMA merge pipeline for the shape merge_pass_any runs
+// at merge tile 2^mlogT.
+template <class K, class V> size_t tma_bytes_at(int mlogT, bool vt8) {
+    switch (mlogT) {
+    case 11:
+        return vt8 ? tma_smem_bytes<K, V, 256, 8, MERGE_STAGES, true>() : tma_smem_bytes<K, V, 128, 16, MERGE_STAGES, true>();
+    case 12:
+        return vt8 ? tma_smem_bytes<K, V, 512, 8, MERGE_STAGES, true>() : tma_smem_bytes<K, V, 256, 16, MERGE_STAGES, true>();
+    default: return tma_smem_bytes<K, V, 512, 16, MERGE_STAGES, true>();
+    }
+}
+
 // Merge-pass shapes: (merge tile log2, keys per consumer thread).  The plain
 // kernel always runs 16 keys per thread.
 template <class K, class V>
@@ -118,6 +130,10 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     // merge tile: at most the sort tile (the plain kernel always uses the sort tile)
     int mlogT = a.merge_tile_log2 ? a.merge_tile_log2 : g.logT;
     if (mlogT > g.logT || mlogT < 11 || a.merge_impl == MERGE_SIMPLE) mlogT = g.logT;
+    if (!a.merge_tile_log2 && a.merge_impl == MERGE_AUTO) {
+        // wide items: shrink the merge tile until the TMA pipeline fits two CTAs per SM
+        while (mlogT > 11 && tma_bytes_at<K, V>(mlogT, a.merge_vt == 8) > TMA_SMEM_AUTO_LIMIT) --mlogT;
+    }
     const int64_t TM = int64_t(1) << mlogT;
 
     if (a.merge_only) {

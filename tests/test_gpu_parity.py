@@ -285,6 +285,35 @@ def test_2e26_int32_dup16_p4096_full_compare(sorter):
     check_keys(sorter, x, 4096)
 
 
+@pytest.mark.parametrize("dist,log2n", [("uniform", 27), ("zipf", 26)])
+def test_pairs_uint64_int32_full_size(sorter, dist, log2n):
+    """The stable-pairs workload at full size (Zipf at 2^26 to bound the host
+    generator's time): the output is the stable sort iff the payload is a
+    permutation, every key travelled with its payload, the keys are
+    nondecreasing and equal keys keep their payload order; sampled ranks are
+    computed by the oracle."""
+    n = 1 << log2n
+    k = W.uniform_uint64(n, seed=W.DEFAULT_SEED) if dist == "uniform" else W.zipf_uint64(n, seed=W.DEFAULT_SEED)
+    v = W.index_payload(n)
+    dk, dv = _to_dev(k), _to_dev(v)
+    ko, vo = sorter.sort_pairs(dk, dv, p=2)
+    sorter.sync()
+    idx = vo.long()
+    assert bool((torch.bincount(idx, minlength=n) == 1).all())
+    assert torch.equal(ko.view(torch.int64), dk.view(torch.int64)[idx])
+    code = ko.view(torch.int64) ^ torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    assert bool((code[1:] >= code[:-1]).all())
+    eq = code[1:] == code[:-1]
+    assert bool((vo[1:][eq] > vo[:-1][eq]).all())
+    got = _to_host(ko)
+    del dk, dv, ko, vo, idx, code, eq
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(1)
+    for i in np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 13)]):
+        lt, le = oracle.rank_bounds(k, int(got[i]))
+        assert lt <= i < le, i
+
+
 def test_2e28_int32_uniform_p2_sampled(sorter):
     """The benchmark's workload: 2^28 uniform int32 keys, p = 2.  Checked by
     properties that hold at any size plus sampled ranks computed by the oracle."""
