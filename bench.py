@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--seg-lo", type=int, default=16)
     ap.add_argument("--seg-hi-log2", type=int, default=17)
     ap.add_argument("--per-array-rounds", type=int, default=2)
-    ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16])
+    ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16, 32])
     ap.add_argument("--merge-tile-log2", type=int, default=0, choices=[0, 11, 12, 13])
     ap.add_argument("--merge-consumer", type=int, default=0, choices=[0, 1])
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
@@ -193,7 +193,7 @@ def workload_name(args) -> str:
 def config(args):
     return {"workload": workload_name(args), "n": 1 << args.log2n, "p": args.p,
             "dist": args.dist, "key_dtype": "int32", "tile_keys": 1 << args.tile_log2,
-            "merge_kernel": args.merge, "merge_vt": args.merge_vt or 16,
+            "merge_kernel": args.merge, "merge_vt": args.merge_vt or 32,
             "merge_tile_keys": 1 << (args.merge_tile_log2 or args.tile_log2),
             "merge_consumer": ["thread sequential merge", "warp bitonic"][args.merge_consumer],
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",

@@ -241,8 +241,10 @@ bs_status bs_graph_destroy(bs_graph *g);
 typedef enum {
     BS_OPT_TILE_LOG2 = 0,    /* value: 11, 12 or 13 (0 = default 12), as bs_set_tile_log2 */
     BS_OPT_MERGE_KERNEL = 1, /* value: a bs_merge_kernel */
-    BS_OPT_MERGE_VT = 2,     /* keys per consumer thread of the TMA merge: 16 (0 = default)
-                                or 8 (twice the threads per tile, tiles <= 4096 keys) */
+    BS_OPT_MERGE_VT = 2,     /* keys per consumer thread of the TMA merge: 8, 16 or 32;
+                                0 (default) = 32 for 32-bit keys alone, 16 otherwise.
+                                Fewer keys per thread = more threads per tile; 8 is
+                                not offered for 8192-key merge tiles (16 is used) */
     BS_OPT_WAIT_LIMIT_MS = 3,/* limit of every device-side wait, ms (0 = default 2000):
                                 a wait that runs out records BS_ERR_TIMEOUT and the
                                 kernel returns, leaving the context usable */

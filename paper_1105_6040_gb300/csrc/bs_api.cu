@@ -163,7 +163,7 @@ struct bs_handle {
     int64_t launches[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
     int logT = 12;
     int merge_impl = MERGE_AUTO;
-    int merge_vt = 16;
+    int merge_vt = 0;         // 0: 32 for 32-bit keys alone, 16 for wider items
     uint64_t wait_ns = 0;  // 0: the kernels' default limit
     int withhold = 0;      // test hook (BS_OPT_TEST_WITHHOLD)
     int schedule = BS_SCHEDULE_TREE;
@@ -827,8 +827,7 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         h->schedule = (int)value;
         return BS_OK;
     case BS_OPT_MERGE_VT:
-        if (value == 0) value = 16;
-        if (value != 8 && value != 16) return BS_ERR_INVALID_ARG;
+        if (value != 0 && value != 8 && value != 16 && value != 32) return BS_ERR_INVALID_ARG;
         h->merge_vt = (int)value;
         return BS_OK;
     default:

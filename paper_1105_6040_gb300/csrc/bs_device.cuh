@@ -1269,15 +1269,17 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
                                  wx);
 }
 
-// Thread consumer of one staged tile (serial merge): lane l of warp w
+// Thread consumer of one staged tile (sequential merge): lane l of warp w
 // produces outputs [d, d + VT) of the tile, d = 32*VT*w + VT*l.  Its
-// merge-path split is found by a binary search inside the warp's split
-// range; then VT steps of the sequential merge each take the smaller head
-// (A's on a tie, which is the stable order, so pairs need no index
-// compares) and load the next item of that run: one shared load and a few
-// integer ops per output.
+// merge-path split comes from a binary search over the tile; then VT steps
+// of the sequential merge each take the smaller head (A's on a tie, which is
+// the stable order, so pairs need no index compares) and load the next item
+// of that run: one shared load and a few integer ops per output.  The warp
+// first writes the largest key just past B's last item (stage slack, past
+// what the copies delivered), so an exhausted B never wins; A's end is
+// tested explicitly.
 template <class K, class V, int VT>
-__device__ __forceinline__ void thread_merge_tile(const K *sa, const K *sb, const V *sav, const V *sbv,
+__device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *sav, const V *sbv,
                                                   int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
                                                   int codec, uint64_t *empty_bar, int tid, K *wk,
                                                   uint32_t *wx) {
@@ -1286,29 +1288,23 @@ __device__ __forceinline__ void thread_merge_tile(const K *sa, const K *sb, cons
     const int lane = tid & 31, w = tid >> 5;
     const int total = na + nb;
     const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
-    int i0, i1;
-    warp_splits<K>(sa, sb, na, nb, d0, d1, lane, i0, i1);
-    const int j0 = d0 - i0, j1 = d1 - i1;
+    if (lane == 0) sb[nb] = max_code<K>();  // every warp writes the same sentinel
+    __syncwarp();
     const int diag = min(d0 + lane * VT, d1);
-    // this lane's split lies in [i0, i1] with diag - i in [j0, j1]
-    int lo = max(i0, diag - j1), hi = min(i1, diag - j0);
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (sb[diag - 1 - mid] < sa[mid]) hi = mid;
-        else lo = mid + 1;
-    }
-    int i = lo;
-    K a = sa[i], b = sb[diag - i];  // past a run's end these are not used
+    const int i_split = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
+    const K *pa = sa + i_split, *pb = sb + (diag - i_split);
+    const K *const a_end = sa + na;
+    K a = *pa, b = *pb;  // a is not used once A is exhausted
     K v[VT];
     uint32_t x[VT];
 #pragma unroll
     for (int u = 0; u < VT; ++u) {
-        const int j = diag + u - i;
-        const bool tb = i >= na || (j < nb && b < a);  // take B's head
+        const bool tb = pa >= a_end || b < a;  // take B's head
         v[u] = tb ? b : a;
-        if constexpr (HV) x[u] = tb ? (uint32_t)(na + j) : (uint32_t)i;
-        i += tb ? 0 : 1;
-        const K nxt = *(tb ? sb + (j + 1) : sa + i);
+        if constexpr (HV) x[u] = tb ? (uint32_t)(na + (pb - sb)) : (uint32_t)(pa - sa);
+        pa += tb ? 0 : 1;
+        pb += tb ? 1 : 0;
+        const K nxt = *(tb ? pb : pa);
         a = tb ? a : nxt;
         b = tb ? nxt : b;
     }
@@ -1449,7 +1445,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
         const StageDesc d = *stage_desc(s);
         if (d.flags & 1) {
             const K *sa = stage_k(s) + d.a_off;
-            const K *sb = stage_k(s) + d.b_off;
+            K *sb = stage_k(s) + d.b_off;
             const int na = d.na, nb = d.nb, total_out = na + nb;
             unsigned char *ws = smem_raw + STAGES * LY::stage + (tid >> 5) * WS::bytes;
             K *dk = (d.flags & 2) ? buf_k1 : buf_k0;

@@ -30,7 +30,7 @@ struct PassArgs {
     const int64_t *ntiles_total;  // device scalar: exact tile count
     int64_t *split;           // per tile merge-path split of the current pass
     int merge_impl;           // MERGE_SIMPLE or MERGE_TMA (the caller checked alignment)
-    int merge_vt;             // keys per consumer thread in the TMA merge: 16, or 8 (twice the warps)
+    int merge_vt;             // keys per consumer thread in the TMA merge: 8, 16, 32 (0: by item size)
     bool merge_only;          // the blocks are caller-sorted runs: no sort phase
     const int64_t *tpp_host;  // merge_only: tiles per pair of each round (host array)
     int oddeven_rounds;       // > 0: after the sort phase, that many compare-split rounds

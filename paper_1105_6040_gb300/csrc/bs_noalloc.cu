@@ -195,7 +195,7 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     a.ntiles_total = tprefix + p;
     a.split = split;
     a.merge_impl = (((uintptr_t)d_out | (uintptr_t)base) & 15) ? bs::MERGE_SIMPLE : bs::MERGE_AUTO;
-    a.merge_vt = 16;
+    a.merge_vt = 0;  // the default shape
     a.merge_only = false;
     a.tpp_host = nullptr;
     a.oddeven_rounds = 0;

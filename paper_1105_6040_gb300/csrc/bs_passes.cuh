@@ -41,77 +41,116 @@ constexpr int MERGE_STAGES = 2;  // stages of the TMA merge pipeline
 constexpr size_t SMEM_OPT_IN_LIMIT = 227 * 1024;
 constexpr int PART_THREADS = 256;  // partition threads per CTA
 
-// One merge pass with merge tiles of MT x MVT keys: merge-path splits, then
-// the TMA pipeline (when allowed and it fits) or the plain kernel.
+// The TMA merge pipeline at shape (MT consumer threads, MVT keys each):
+// launches it and returns 1, or returns 0 when it cannot run here (shared
+// memory, or above the automatic limit) so the caller runs the plain kernel.
 template <class K, class V, int MT, int MVT>
-bool merge_pass(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
-    constexpr int STAGES = MERGE_STAGES;
-    constexpr int TM = MT * MVT;
-    constexpr size_t smem = smem_bytes<K, V>(TM);
-    auto mk = merge_kernel<K, V, MT, MVT>;
+int launch_merge_tma(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
     const int ci = a.merge_consumer == 1 ? 1 : 0;  // 1: warp bitonic consumers
-    auto mt = ci ? merge_tma_kernel<K, V, MT, MVT, STAGES, true> : merge_tma_kernel<K, V, MT, MVT, STAGES, false>;
-    const size_t msmem = tma_smem_bytes<K, V, MT, MVT, STAGES, true>();
-    auto pk = partition_kernel<K>;
-    static std::atomic<int> occ_mk{0}, occ_mt[2] = {{0}, {0}};
-    if (!occ_mk.load()) {
-        if (!allow_smem(mk, smem)) return false;
-        occ_mk.store(resident_ctas(mk, MT, smem));
-    }
+    auto mt = ci ? merge_tma_kernel<K, V, MT, MVT, MERGE_STAGES, true>
+                 : merge_tma_kernel<K, V, MT, MVT, MERGE_STAGES, false>;
+    constexpr size_t msmem = tma_smem_bytes<K, V, MT, MVT, MERGE_STAGES, true>();
+    static std::atomic<int> occ_mt[2] = {{0}, {0}};
     if (!occ_mt[ci].load()) {
         if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem))
             occ_mt[ci].store(resident_ctas(mt, MT + 32, msmem));
         else
             occ_mt[ci].store(-1);
     }
-    bool tma = false;
-    if (occ_mt[ci].load() > 0) {
-        if (a.merge_impl == MERGE_TMA) tma = true;
-        else if (a.merge_impl == MERGE_AUTO) tma = msmem <= TMA_SMEM_AUTO_LIMIT;
-    }
-    (void)TM;
+    if (occ_mt[ci].load() <= 0) return 0;
+    if (a.merge_impl == MERGE_AUTO && msmem > TMA_SMEM_AUTO_LIMIT) return 0;
     const Geo &g = a.g;
-    K *k0 = (K *)a.k0, *k1 = (K *)a.k1;
-    V *v0 = (V *)a.v0, *v1 = (V *)a.v1;
-    L.begin(L.owner, CLS_PARTITION, L.stream);
-    pk<<<(unsigned)grid_for((tiles + PART_THREADS - 1) / PART_THREADS, (int64_t)L.sms * 8), PART_THREADS,
-         0, L.stream>>>(g, lvl, k0, k1, a.split, a.ntiles_total);
-    if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
-    L.begin(L.owner, CLS_MERGE, L.stream);
-    if (tma)
-        mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt[ci]), MT + 32, msmem, L.stream>>>(
-            g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-    else
-        mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream>>>(
-            g, lvl, k0, k1, v0, v1, a.codec, a.split, a.ntiles_total);
-    return L.end(L.owner, CLS_MERGE, L.stream);
+    mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt[ci]), MT + 32, msmem, L.stream>>>(
+        g, lvl, (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, a.split, a.ntiles_total);
+    return 1;
+}
+
+// The plain merge kernel (any alignment, any item size) at shape (MT, MVT).
+template <class K, class V, int MT, int MVT>
+bool launch_merge_plain(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
+    constexpr size_t smem = smem_bytes<K, V>(MT * MVT);
+    auto mk = merge_kernel<K, V, MT, MVT>;
+    static std::atomic<int> occ_mk{0};
+    if (!occ_mk.load()) {
+        if (!allow_smem(mk, smem)) return false;
+        occ_mk.store(resident_ctas(mk, MT, smem));
+    }
+    const Geo &g = a.g;
+    mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream>>>(
+        g, lvl, (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, a.split, a.ntiles_total);
+    return true;
+}
+
+// Keys per consumer thread of the TMA merge: the option, else 32 for 32-bit
+// keys alone and 16 for wider items (register budget).
+template <class K, class V> int merge_vt_of(const PassArgs &a) {
+    if (a.merge_vt) return a.merge_vt;
+    return (sizeof(K) == 4 && !HasVal<V>::value) ? 32 : 16;
 }
 
 // Shared memory of the TMA merge pipeline for the shape merge_pass_any runs
-// at merge tile 2^mlogT.
-template <class K, class V> size_t tma_bytes_at(int mlogT, bool vt8) {
+// at merge tile 2^mlogT with vt keys per consumer thread.
+template <class K, class V> size_t tma_bytes_at(int mlogT, int vt) {
     switch (mlogT) {
     case 11:
-        return vt8 ? tma_smem_bytes<K, V, 256, 8, MERGE_STAGES, true>() : tma_smem_bytes<K, V, 128, 16, MERGE_STAGES, true>();
+        return vt == 8    ? tma_smem_bytes<K, V, 256, 8, MERGE_STAGES, true>()
+               : vt == 16 ? tma_smem_bytes<K, V, 128, 16, MERGE_STAGES, true>()
+                          : tma_smem_bytes<K, V, 64, 32, MERGE_STAGES, true>();
     case 12:
-        return vt8 ? tma_smem_bytes<K, V, 512, 8, MERGE_STAGES, true>() : tma_smem_bytes<K, V, 256, 16, MERGE_STAGES, true>();
-    default: return tma_smem_bytes<K, V, 512, 16, MERGE_STAGES, true>();
+        return vt == 8    ? tma_smem_bytes<K, V, 512, 8, MERGE_STAGES, true>()
+               : vt == 16 ? tma_smem_bytes<K, V, 256, 16, MERGE_STAGES, true>()
+                          : tma_smem_bytes<K, V, 128, 32, MERGE_STAGES, true>();
+    default:
+        return vt == 32 ? tma_smem_bytes<K, V, 256, 32, MERGE_STAGES, true>()
+                        : tma_smem_bytes<K, V, 512, 16, MERGE_STAGES, true>();
     }
 }
 
-// Merge-pass shapes: (merge tile log2, keys per consumer thread).  The plain
-// kernel always runs 16 keys per thread.
+// One merge pass with merge tiles of 2^mlogT keys: merge-path splits, then
+// the TMA pipeline (shape by keys per consumer thread: 8, 16 or 32; 8 is
+// not offered for 8192-key tiles) where allowed and it fits, else the plain
+// kernel at 16 keys per thread.
 template <class K, class V>
 bool merge_pass_any(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
-    const bool vt8 = a.merge_vt == 8 && a.merge_impl != MERGE_SIMPLE;
-    switch (lvl.mlogT) {
-    case 11:
-        return vt8 ? merge_pass<K, V, 256, 8>(a, L, lvl, tiles) : merge_pass<K, V, 128, 16>(a, L, lvl, tiles);
-    case 12:
-        return vt8 ? merge_pass<K, V, 512, 8>(a, L, lvl, tiles) : merge_pass<K, V, 256, 16>(a, L, lvl, tiles);
-    case 13: return merge_pass<K, V, 512, 16>(a, L, lvl, tiles);
-    default: return false;
+    const Geo &g = a.g;
+    L.begin(L.owner, CLS_PARTITION, L.stream);
+    partition_kernel<K><<<(unsigned)grid_for((tiles + PART_THREADS - 1) / PART_THREADS, (int64_t)L.sms * 8),
+                          PART_THREADS, 0, L.stream>>>(g, lvl, (const K *)a.k0, (const K *)a.k1, a.split,
+                                                       a.ntiles_total);
+    if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
+    L.begin(L.owner, CLS_MERGE, L.stream);
+    int done = 0;
+    if (a.merge_impl != MERGE_SIMPLE) {
+        const int vt = merge_vt_of<K, V>(a);
+        switch (lvl.mlogT) {
+        case 11:
+            done = vt == 8    ? launch_merge_tma<K, V, 256, 8>(a, L, lvl, tiles)
+                   : vt == 16 ? launch_merge_tma<K, V, 128, 16>(a, L, lvl, tiles)
+                              : launch_merge_tma<K, V, 64, 32>(a, L, lvl, tiles);
+            break;
+        case 12:
+            done = vt == 8    ? launch_merge_tma<K, V, 512, 8>(a, L, lvl, tiles)
+                   : vt == 16 ? launch_merge_tma<K, V, 256, 16>(a, L, lvl, tiles)
+                              : launch_merge_tma<K, V, 128, 32>(a, L, lvl, tiles);
+            break;
+        case 13:
+            done = vt == 32 ? launch_merge_tma<K, V, 256, 32>(a, L, lvl, tiles)
+                            : launch_merge_tma<K, V, 512, 16>(a, L, lvl, tiles);
+            break;
+        default: return false;
+        }
     }
+    if (!done) {
+        bool ok;
+        switch (lvl.mlogT) {
+        case 11: ok = launch_merge_plain<K, V, 128, 16>(a, L, lvl, tiles); break;
+        case 12: ok = launch_merge_plain<K, V, 256, 16>(a, L, lvl, tiles); break;
+        case 13: ok = launch_merge_plain<K, V, 512, 16>(a, L, lvl, tiles); break;
+        default: return false;
+        }
+        if (!ok) return false;
+    }
+    return L.end(L.owner, CLS_MERGE, L.stream);
 }
 
 template <class K, class V, int THREADS, int KPT>
@@ -132,7 +171,7 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     if (mlogT > g.logT || mlogT < 11 || a.merge_impl == MERGE_SIMPLE) mlogT = g.logT;
     if (!a.merge_tile_log2 && a.merge_impl == MERGE_AUTO) {
         // wide items: shrink the merge tile until the TMA pipeline fits two CTAs per SM
-        while (mlogT > 11 && tma_bytes_at<K, V>(mlogT, a.merge_vt == 8) > TMA_SMEM_AUTO_LIMIT) --mlogT;
+        while (mlogT > 11 && tma_bytes_at<K, V>(mlogT, merge_vt_of<K, V>(a)) > TMA_SMEM_AUTO_LIMIT) --mlogT;
     }
     const int64_t TM = int64_t(1) << mlogT;
 

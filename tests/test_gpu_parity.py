@@ -340,7 +340,8 @@ def test_2e28_int32_uniform_p2_sampled(sorter):
 @pytest.mark.parametrize("merge_kernel,merge_vt,tile_log2,merge_tile_log2,consumer", [
     ("simple", 0, 12, 0, 0), ("tma", 16, 12, 0, 0), ("tma", 8, 12, 0, 0), ("tma", 16, 12, 11, 0),
     ("tma", 8, 12, 11, 0), ("tma", 16, 13, 11, 0), ("tma", 16, 13, 12, 0), ("auto", 0, 11, 11, 0),
-    ("tma", 16, 12, 0, 1), ("tma", 8, 13, 12, 1)])
+    ("tma", 16, 12, 0, 1), ("tma", 8, 13, 12, 1), ("tma", 32, 12, 0, 0), ("tma", 32, 13, 0, 0),
+    ("tma", 32, 12, 11, 1), ("tma", 32, 13, 13, 1)])
 def test_merge_kernel_variants(merge_kernel, merge_vt, tile_log2, merge_tile_log2, consumer):
     """Every merge-pass kernel, consumer and merge-tile shape gives the
     oracle's output on every key/value type, ragged sizes, several p and
@@ -372,7 +373,7 @@ def test_merge_kernel_variants(merge_kernel, merge_vt, tile_log2, merge_tile_log
         s.close()
 
 
-@pytest.mark.parametrize("merge_vt,consumer", [(8, 1), (16, 1), (8, 0), (16, 0)])
+@pytest.mark.parametrize("merge_vt,consumer", [(8, 1), (16, 1), (32, 1), (8, 0), (16, 0), (32, 0)])
 def test_merge_stage_reuse_repeated(merge_vt, consumer):
     """Stress for the TMA pipeline's stage ring: many short segmented merges,
     run ten times; every run must equal the oracle.  A consumer read that is
