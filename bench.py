@@ -53,12 +53,13 @@ def parse_args():
                          "arrays of log-uniform length in one graph-captured segmented sort")
     ap.add_argument("--pairs-log2n", type=int, default=27)
     ap.add_argument("--pairs-dist", default="uniform", choices=["uniform", "zipf"])
+    ap.add_argument("--pairs-tile-log2", type=int, default=12)
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--seg-lo", type=int, default=16)
     ap.add_argument("--seg-hi-log2", type=int, default=17)
     ap.add_argument("--per-array-rounds", type=int, default=2)
     ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16, 32])
-    ap.add_argument("--merge-tile-log2", type=int, default=0, choices=[0, 11, 12, 13])
+    ap.add_argument("--merge-tile-log2", type=int, default=12, choices=[0, 11, 12, 13])
     ap.add_argument("--merge-consumer", type=int, default=0, choices=[0, 1])
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
@@ -66,7 +67,9 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
-    ap.add_argument("--tile-log2", type=int, default=12)
+    ap.add_argument("--tile-log2", type=int, default=13,
+                    help="sort-phase tile 2^k keys (the bench default: 8192-key sort tiles, "
+                         "merged in 4096-key merge tiles)")
     ap.add_argument("--merge", choices=["auto", "simple", "tma"], default="auto",
                     help="merge-pass kernel (auto: TMA pipeline where it fits)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -418,8 +421,8 @@ def run_pairs(args):
     keys_h = (W.uniform_uint64(n, seed=SEED) if args.pairs_dist == "uniform"
               else W.zipf_uint64(n, seed=SEED))
     vals_h = W.index_payload(n)
-    sorter = abi.Sorter(0, tile_log2=args.tile_log2, merge_kernel=args.merge, merge_vt=args.merge_vt,
-                        merge_tile_log2=args.merge_tile_log2, merge_consumer=args.merge_consumer)
+    sorter = abi.Sorter(0, tile_log2=args.pairs_tile_log2, merge_kernel=args.merge, merge_vt=args.merge_vt,
+                        merge_consumer=args.merge_consumer)  # merge tile: the library's choice
     dk, dv = torch.from_numpy(keys_h).cuda(), torch.from_numpy(vals_h).cuda()
     ko, vo = torch.empty_like(dk), torch.empty_like(dv)
     stream = torch.cuda.current_stream()
@@ -480,7 +483,7 @@ def run_pairs(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+i32", "data": "synthetic",
         "config": {"workload": f"stable pair sort, 2^{args.pairs_log2n} {args.pairs_dist} uint64 keys + int32 "
                                f"index payload, p={args.p} blocks", "n": n, "p": args.p,
-                   "dist": args.pairs_dist, "tile_keys": 1 << args.tile_log2, "seed": SEED,
+                   "dist": args.pairs_dist, "tile_keys": 1 << args.pairs_tile_log2, "seed": SEED,
                    "l2": "inputs (12 B x n = 1.5 GiB at 2^27) larger than the 129 MB L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": kernels[dom]["gbs"] / peak, "traffic": None,
@@ -658,7 +661,7 @@ def run_psweep(args):
     stream = torch.cuda.current_stream()
     for sched in ("tree", "oddeven"):
         ps = [1 << i for i in range(13)] if sched == "tree" else [1, 2, 4, 8, 16, 32, 64]
-        s = abi.Sorter(local, tile_log2=args.tile_log2)
+        s = abi.Sorter(local, tile_log2=12)  # the 4096-key tile every row of this table uses
         abi.bs_set_option(s.h, "merge_schedule", sched)
         for p in ps:
             for _ in range(2):
@@ -701,7 +704,7 @@ def run_localsort(args):
     out = torch.empty_like(x)
     rows = []
     for ls in ("merge", "quick", "bubble"):
-        s = abi.Sorter(local, tile_log2=args.tile_log2)
+        s = abi.Sorter(local, tile_log2=12)  # the 4096-key tile every row of this table uses
         abi.bs_set_option(s.h, "local_sort", ls)
         s.sort_keys(x, out=out, p=args.p)
         s.sync()

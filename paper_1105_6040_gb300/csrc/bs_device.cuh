@@ -324,6 +324,50 @@ __device__ __forceinline__ void cand_merge_pairs(const K *sk, const uint32_t *sx
     bitonic_merge_pairs<VT>(out, oi);
 }
 
+// Sequential merge of KPT outputs from two sorted lists in padded shared
+// memory, A = S[a0, a0+m) and B = S[b0, b0+m), starting at the merge-path
+// split (i, j): each step takes the smaller head (A's on a tie) and loads
+// the next item of that list -- one shared load per output.  Reads stay in
+// [a0, b0 + m]: one past a list's end is read but not used.
+template <class K, int KPT>
+__device__ __forceinline__ void seq_merge_keys(const K *sk, int a0, int b0, int m, int i, int j, K (&out)[KPT]) {
+    K a = sk[spad<K>(a0 + i)], b = sk[spad<K>(b0 + j)];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+        const bool tb = i >= m || (j < m && b < a);  // take B's head
+        out[u] = tb ? b : a;
+        i += tb ? 0 : 1;
+        j += tb ? 1 : 0;
+        const K nxt = sk[spad<K>(tb ? b0 + j : a0 + i)];
+        a = tb ? a : nxt;
+        b = tb ? nxt : b;
+    }
+}
+
+// The same for pairs, ordered by (code, original position) as every pair
+// network here is; oi[] receives the positions.
+template <class K, int KPT>
+__device__ __forceinline__ void seq_merge_pairs(const K *sk, const uint32_t *sx, int a0, int b0, int m, int i,
+                                                int j, K (&out)[KPT], uint32_t (&oi)[KPT]) {
+    K a = sk[spad<K>(a0 + i)], b = sk[spad<K>(b0 + j)];
+    uint32_t xa = sx[spad<uint32_t>(a0 + i)], xb = sx[spad<uint32_t>(b0 + j)];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+        const bool tb = i >= m || (j < m && ki_less(b, xb, a, xa));
+        out[u] = tb ? b : a;
+        oi[u] = tb ? xb : xa;
+        i += tb ? 0 : 1;
+        j += tb ? 1 : 0;
+        const int at = tb ? b0 + j : a0 + i;
+        const K nxt = sk[spad<K>(at)];
+        const uint32_t nx = sx[spad<uint32_t>(at)];
+        a = tb ? a : nxt;
+        xa = tb ? xa : nx;
+        b = tb ? nxt : b;
+        xb = tb ? nx : xb;
+    }
+}
+
 // ---------------------------------------------------------------- tile sort
 
 // Shared memory of the tile sort: codes, then (pairs) original positions and
@@ -333,11 +377,19 @@ template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes
            (sizeof(V) > 1 ? smem_val_offset<uint32_t>(T) + sizeof(V) * (size_t)spad_size<V>(T) : 0);
 }
 
+// Merge rounds of the keys-only tile sort done with register shuffles
+// inside a warp before the shared-memory rounds take over.
+#ifndef TILE_SHUFFLE_ROUNDS
+#define TILE_SHUFFLE_ROUNDS 4
+#endif
+
 // Tile sort (the sort phase of Fig. 1 at CTA scale).  Tile t covers
 // keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
-// KPT keys in registers, then log2(THREADS) rounds merge pairs of sorted
-// lists through shared memory (merge-path split + candidate merge); rounds
-// whose lists live inside one warp synchronise only that warp.  Pairs sort
+// KPT keys in registers; keys-only tiles then merge pairs of lists with
+// TILE_SHUFFLE_ROUNDS warp-shuffle rounds, and the remaining rounds merge
+// through shared memory (merge-path split + sequential merge of KPT
+// outputs per thread); rounds whose lists live inside one warp synchronise
+// only that warp.  Pairs sort
 // (code, original position), which is the stable order; values move once,
 // at the final store.  The sorted tile is written -- decoded if this is the
 // segment's last pass -- to the buffer its merge schedule starts from.
@@ -395,10 +447,11 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
 
         int r0 = 0;
         if constexpr (!HV) {
-            // merges inside a warp: register shuffles, no shared memory
+            // the first merges inside a warp: register shuffles, no shared memory
             const int lane = tid & 31;
 #pragma unroll 1
-            for (; (2 << r0) <= 32 && (KPT << r0) < T; ++r0) warp_merge_round<KPT>(k, r0, lane);
+            for (; r0 < TILE_SHUFFLE_ROUNDS && (2 << r0) <= 32 && (KPT << r0) < T; ++r0)
+                warp_merge_round<KPT>(k, r0, lane);
         }
 #pragma unroll 1
         for (int r = r0; (KPT << r) < T; ++r) {
@@ -418,12 +471,12 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
                     return ki_less(sk[spad<K>(b0 + ib)], sx[spad<uint32_t>(b0 + ib)],
                                    sk[spad<K>(a0 + ia)], sx[spad<uint32_t>(a0 + ia)]);
                 });
-                cand_merge_pairs<K, KPT>(sk, sx, a0, m, b0, m, i, diag - i, k, x);
+                seq_merge_pairs<K, KPT>(sk, sx, a0, b0, m, i, diag - i, k, x);
             } else {
                 const int i = merge_path_pred<int>(m, m, diag, [&](int ia, int ib) {
                     return sk[spad<K>(b0 + ib)] < sk[spad<K>(a0 + ia)];
                 });
-                cand_merge_keys<K, KPT>(sk, a0, m, b0, m, i, diag - i, k);
+                seq_merge_keys<K, KPT>(sk, a0, b0, m, i, diag - i, k);
             }
             if (warp_round) __syncwarp();
             else __syncthreads();
