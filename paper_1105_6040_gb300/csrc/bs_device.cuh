@@ -855,10 +855,11 @@ __device__ __forceinline__ int64_t level_tiles(const Geo &g, const Level &L,
 }
 
 // Merge-path split (absolute A index) at the start of every active tile, one
-// thread per tile (a binary search).  On 2^28 keys this beat 4, 8 or 32
-// lanes per tile running a (lanes+1)-way search (0.047 ms a pass against
-// 0.065 to 0.13 ms): the wider search needs fewer rounds of dependent loads
-// but issues several times as many loads.
+// thread per tile (a binary search).  On 2^28 keys this beat both wider
+// searches tried: 4, 8 or 32 lanes per tile running a (lanes+1)-way search
+// (0.065 to 0.13 ms a pass against 0.047 ms) and one thread probing three
+// quartiles per step (0.053 ms): fewer rounds of dependent loads do not pay
+// for the extra loads.
 template <class K>
 __global__ void partition_kernel(Geo g, Level L, const K *buf0, const K *buf1, int64_t *split,
                                  const int64_t *__restrict__ ntiles_total) {
@@ -1144,35 +1145,20 @@ __device__ __forceinline__ void warp_splits(const K *sa, const K *sb, int na, in
     i1 = __shfl_sync(0xffffffffu, lo, 16);
 }
 
-// Stores a warp's 32*VT merged outputs, held lane-blocked (lane l has
-// outputs VT*l .. VT*l + VT - 1; for pairs x[] holds their staging indices,
-// A's first, then B's from na).  A transpose through the warp's scratch
-// hands lane l the 16-byte chunks l, l+32, .. so that every store
-// instruction writes 512 contiguous bytes; pairs fetch their values from the
-// stage by index and then release it (keys-only callers release it before).
-// cnt = valid outputs, o = global index of the first.
+// Emits a warp's 32*VT merged outputs held chunk-striped: lane l has the
+// 16-byte chunks l, l+32, .. (chunk m of the lane in registers m*E ..
+// m*E + E-1; for pairs x[] holds their staging indices, A's first, then
+// B's from na), so every store instruction writes 512 contiguous bytes.
+// Pairs fetch their values from the stage by index and then release it
+// (keys-only callers release it before).  cnt = valid outputs, o = global
+// index of the first.
 template <class K, class V, int VT>
-__device__ __forceinline__ void store_warp_outputs(K (&v)[VT], uint32_t (&x)[VT], const V *sav, const V *sbv,
-                                                   int na, K *dk, V *dv, int64_t o, int cnt, bool fin, int codec,
-                                                   uint64_t *empty_bar, int lane, K *wk, uint32_t *wx) {
+__device__ __forceinline__ void emit_chunk_striped(K (&v)[VT], const uint32_t (&x)[VT], const V *sav,
+                                                   const V *sbv, int na, K *dk, V *dv, int64_t o, int cnt,
+                                                   bool fin, int codec, uint64_t *empty_bar, int lane) {
     constexpr bool HV = HasVal<V>::value;
     constexpr int E = 16 / (int)sizeof(K);  // keys per 16-byte chunk
     constexpr int C = VT / E;               // chunks per lane
-    static_assert(C >= 1 && VT % E == 0, "whole chunks per lane");
-#pragma unroll
-    for (int r = 0; r < C; ++r) {
-        const int at = swz_chunk(C * lane + r) * E;
-        st_chunk<K, E>(wk + at, v + r * E);
-        if constexpr (HV) st_chunk<uint32_t, E>(wx + at, x + r * E);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < C; ++m) {
-        const int at = swz_chunk(32 * m + lane) * E;
-        ld_chunk<K, E>(wk + at, v + m * E);
-        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + m * E);
-    }
-    __syncwarp();  // the scratch is free for the warp's next tile
     V vals[VT];
     if constexpr (HV) {
 #pragma unroll
@@ -1205,6 +1191,68 @@ __device__ __forceinline__ void store_warp_outputs(K (&v)[VT], uint32_t (&x)[VT]
                 if (eb + p < cnt) dv[o + eb + p] = vals[m * E + p];
         }
     }
+}
+
+// Stores a warp's 32*VT merged outputs held lane-blocked (lane l has
+// outputs VT*l .. VT*l + VT - 1): a transpose through the warp's XOR-swizzled
+// scratch makes them chunk-striped, then emit_chunk_striped stores them.
+template <class K, class V, int VT>
+__device__ __forceinline__ void store_warp_outputs(K (&v)[VT], uint32_t (&x)[VT], const V *sav, const V *sbv,
+                                                   int na, K *dk, V *dv, int64_t o, int cnt, bool fin, int codec,
+                                                   uint64_t *empty_bar, int lane, K *wk, uint32_t *wx) {
+    constexpr bool HV = HasVal<V>::value;
+    constexpr int E = 16 / (int)sizeof(K);
+    constexpr int C = VT / E;
+    static_assert(C >= 1 && VT % E == 0, "whole chunks per lane");
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        const int at = swz_chunk(C * lane + r) * E;
+        st_chunk<K, E>(wk + at, v + r * E);
+        if constexpr (HV) st_chunk<uint32_t, E>(wx + at, x + r * E);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int at = swz_chunk(32 * m + lane) * E;
+        ld_chunk<K, E>(wk + at, v + m * E);
+        if constexpr (HV) ld_chunk<uint32_t, E>(wx + at, x + m * E);
+    }
+    __syncwarp();  // the scratch is free for the warp's next tile
+    emit_chunk_striped<K, V, VT>(v, x, sav, sbv, na, dk, dv, o, cnt, fin, codec, empty_bar, lane);
+}
+
+// The same for outputs held S apart (S odd, S = VT + 1): lane l has outputs
+// S*l .. S*l + S - 1 below 32*VT (the last lane the remainder).  The odd
+// stride makes the scalar scratch writes conflict-free without a swizzle;
+// the chunk reads are contiguous across lanes.
+template <class K, class V, int VT, int S>
+__device__ __forceinline__ void store_warp_outputs_spaced(const K (&v)[S], const uint32_t (&x)[S], const V *sav,
+                                                          const V *sbv, int na, K *dk, V *dv, int64_t o, int cnt,
+                                                          bool fin, int codec, uint64_t *empty_bar, int lane,
+                                                          K *wk, uint32_t *wx) {
+    constexpr bool HV = HasVal<V>::value;
+    constexpr int WO = 32 * VT;
+    constexpr int E = 16 / (int)sizeof(K);
+    constexpr int C = VT / E;
+    static_assert(S % 2 == 1 && 31 * S <= WO, "odd spacing, the last lane keeps at least nothing");
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const int e = lane * S + q;
+        if (e < WO) {
+            wk[e] = v[q];
+            if constexpr (HV) wx[e] = x[q];
+        }
+    }
+    __syncwarp();
+    K c[VT];
+    uint32_t cx[VT];
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        ld_chunk<K, E>(wk + (32 * m + lane) * E, c + m * E);
+        if constexpr (HV) ld_chunk<uint32_t, E>(wx + (32 * m + lane) * E, cx + m * E);
+    }
+    __syncwarp();  // the scratch is free for the warp's next tile
+    emit_chunk_striped<K, V, VT>(c, cx, sav, sbv, na, dk, dv, o, cnt, fin, codec, empty_bar, lane);
 }
 
 // Warp consumer of one staged tile (bitonic): warp w produces outputs
@@ -1343,15 +1391,48 @@ __device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *s
     const int d0 = min(w * WO, total), d1 = min(d0 + WO, total);
     if (lane == 0) sb[nb] = max_code<K>();  // every warp writes the same sentinel
     __syncwarp();
-    const int diag = min(d0 + lane * VT, d1);
+    // outputs per lane: VT, or VT + 1 (odd) when VT >= 31 -- lanes whose
+    // sequential reads advance in step then sit an odd distance apart, in
+    // distinct banks (the last lane takes the remainder)
+    constexpr int S = VT >= 31 ? VT + 1 : VT;
+    const int diag = min(d0 + lane * S, d1);
     const int i_split = merge_path_pred<int>(na, nb, diag, [&](int ia, int ib) { return sb[ib] < sa[ia]; });
+    // A warp whose outputs all come from one run (sorted or reversed input,
+    // long runs of equal keys) copies them instead: its lanes' sequential
+    // reads would sit VT items apart, all in one or two shared-memory banks.
+    {
+        const int i0 = __shfl_sync(0xffffffffu, i_split, 0), j0 = d0 - i0, wn = d1 - d0;
+        const bool all_a = wn > 0 && i0 + wn <= na && (j0 >= nb || !(sb[j0] < sa[i0 + wn - 1]));
+        const bool all_b = wn > 0 && !all_a && j0 + wn <= nb && (i0 >= na || sb[j0 + wn - 1] < sa[i0]);
+        if (all_a || all_b) {
+            const K *src = all_a ? sa + i0 : sb + j0;
+            const V *srcv = all_a ? sav + i0 : sbv + j0;
+            K *out = dk + o_lo + d0;
+            V *outv = dv + o_lo + d0;
+            if (fin) {
+#pragma unroll 4
+                for (int e = lane; e < wn; e += 32) {
+                    out[e] = dec_code(src[e], codec);
+                    if constexpr (HV) outv[e] = srcv[e];
+                }
+            } else {
+#pragma unroll 4
+                for (int e = lane; e < wn; e += 32) {
+                    out[e] = src[e];
+                    if constexpr (HV) outv[e] = srcv[e];
+                }
+            }
+            mbar_arrive(empty_bar);  // every shared read of this stage is done
+            return;
+        }
+    }
     const K *pa = sa + i_split, *pb = sb + (diag - i_split);
     const K *const a_end = sa + na;
     K a = *pa, b = *pb;  // a is not used once A is exhausted
-    K v[VT];
-    uint32_t x[VT];
+    K v[S];
+    uint32_t x[S];
 #pragma unroll
-    for (int u = 0; u < VT; ++u) {
+    for (int u = 0; u < S; ++u) {
         const bool tb = pa >= a_end || b < a;  // take B's head
         v[u] = tb ? b : a;
         if constexpr (HV) x[u] = tb ? (uint32_t)(na + (pb - sb)) : (uint32_t)(pa - sa);
@@ -1362,8 +1443,12 @@ __device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *s
         b = tb ? nxt : b;
     }
     if constexpr (!HV) mbar_arrive(empty_bar);  // every shared read of this stage is done
-    store_warp_outputs<K, V, VT>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec, empty_bar, lane, wk,
-                                 wx);
+    if constexpr (S == VT)
+        store_warp_outputs<K, V, VT>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec, empty_bar, lane,
+                                     wk, wx);
+    else
+        store_warp_outputs_spaced<K, V, VT, S>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec,
+                                               empty_bar, lane, wk, wx);
 }
 
 // Merge pass with a TMA pipeline (warp specialised, persistent).  The last
