@@ -185,35 +185,36 @@ __device__ __forceinline__ void cas_pairs(K &a, uint32_t &ai, K &b, uint32_t &bi
     bi = sw ? i : bi;
 }
 
-// Bitonic sorting network over N registers, ascending (Batcher 1968).
+// Odd-even merge sorting network over N registers, ascending (Batcher 1968),
+// in Knuth's iterative form: for each merge size 2p and comparator distance
+// q = p, p/2, .., 1, compare i+j with i+j+q when both lie in the same block
+// of 2p.  63 comparators for N = 16 (bitonic sorting takes 80).  The list
+// is built at compile time, so the unrolled network indexes registers only.
+template <int N> struct OddEvenNet {
+    int a[N * N], b[N * N], n;
+    constexpr OddEvenNet() : a(), b(), n(0) {
+        for (int p = 1; p < N; p <<= 1)
+            for (int q = p; q >= 1; q >>= 1)
+                for (int j = q % p; j + q < N; j += 2 * q)
+                    for (int i = 0; i < q && i < N - j - q; ++i)
+                        if ((i + j) / (2 * p) == (i + j + q) / (2 * p)) {
+                            a[n] = i + j;
+                            b[n] = i + j + q;
+                            ++n;
+                        }
+    }
+};
+
 template <int N, class K> __device__ __forceinline__ void reg_sort_keys(K (&k)[N]) {
+    constexpr OddEvenNet<N> net{};
 #pragma unroll
-    for (int size = 2; size <= N; size <<= 1)
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    if ((i & size) == 0) cas_keys(k[i], k[j]);
-                    else cas_keys(k[j], k[i]);
-                }
-            }
+    for (int c = 0; c < net.n; ++c) cas_keys(k[net.a[c]], k[net.b[c]]);
 }
 
 template <int N, class K> __device__ __forceinline__ void reg_sort_pairs(K (&k)[N], uint32_t (&x)[N]) {
+    constexpr OddEvenNet<N> net{};
 #pragma unroll
-    for (int size = 2; size <= N; size <<= 1)
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    if ((i & size) == 0) cas_pairs(k[i], x[i], k[j], x[j]);
-                    else cas_pairs(k[j], x[j], k[i], x[i]);
-                }
-            }
+    for (int c = 0; c < net.n; ++c) cas_pairs(k[net.a[c]], x[net.a[c]], k[net.b[c]], x[net.b[c]]);
 }
 
 // Ascending bitonic merge of a bitonic sequence held in N registers.
@@ -260,14 +261,17 @@ template <int N, class K> __device__ __forceinline__ void warp_merge_round(K (&k
     K t[N];
 #pragma unroll
     for (int u = 0; u < N; ++u) t[u] = shfl_xor_k<N>(k[N - 1 - u], (2 << r) - 1);
+    // the lower lane keeps the smaller key, the upper the larger: take the
+    // partner's key when (partner < own) differs from "upper" (one compare
+    // and one select per key)
 #pragma unroll
-    for (int u = 0; u < N; ++u) k[u] = upper ? (k[u] < t[u] ? t[u] : k[u]) : (k[u] < t[u] ? k[u] : t[u]);
+    for (int u = 0; u < N; ++u) k[u] = ((t[u] < k[u]) != upper) ? t[u] : k[u];
     for (int ls = (1 << r) >> 1; ls > 0; ls >>= 1) {
         const bool up = lane & ls;
 #pragma unroll
         for (int u = 0; u < N; ++u) {
             const K p = shfl_xor_k<N>(k[u], ls);
-            k[u] = up ? (k[u] < p ? p : k[u]) : (k[u] < p ? k[u] : p);
+            k[u] = ((p < k[u]) != up) ? p : k[u];
         }
     }
     bitonic_merge_keys<N>(k);
@@ -1351,7 +1355,7 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
                 v[q] = take ? pk : v[q];
                 x[q] = take ? px : x[q];
             } else {
-                v[q] = up ? (v[q] < pk ? pk : v[q]) : (v[q] < pk ? v[q] : pk);
+                v[q] = ((pk < v[q]) != up) ? pk : v[q];
             }
         }
     }
