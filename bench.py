@@ -374,7 +374,9 @@ def run_ours(args):
         assert np.all(h_out.numpy()[1:] >= h_out.numpy()[:-1])
         e2e = {"value": world * n * args.e2e_steps / float(dt.item()) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
-               "api": "bs_sort_keys_host (pinned host buffers)", "steps": args.e2e_steps}
+               "api": "bs_sort_keys_host (page-locked host buffers: the sort phase reads the input "
+                      "and the last merge pass writes the output across the host link)",
+               "steps": args.e2e_steps}
         del h_in, h_out
 
     sorter.close()

@@ -159,9 +159,13 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
 
 /*
  * Host-memory convenience: sort n keys from host buffer h_in into host
- * buffer h_out (may be equal), copying through the handle's device buffers
- * on the handle's internal stream; returns after the result is in h_out.
- * Page-locked host buffers give the fastest copies.  Errors as bs_sort_keys.
+ * buffer h_out (may be equal) on the handle's internal stream; returns after
+ * the result is in h_out.  When both buffers are page-locked (or registered)
+ * and mapped into the GPU's address space -- the coherent host link of a
+ * Grace-Blackwell node -- the sort phase reads h_in and the last merge pass
+ * writes h_out directly, and every other pass stays in device memory;
+ * otherwise (or with BS_OPT_HOST_DIRECT = 0) the keys are copied in, sorted
+ * and copied out.  Errors as bs_sort_keys.
  */
 bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n,
                             bs_dtype kt, int64_t p);
@@ -258,10 +262,13 @@ typedef enum {
     BS_OPT_MERGE_TILE_LOG2 = 7,/* merge-pass tile 2^value keys: 0 (default) = the sort tile,
                                 or 11 .. the sort tile's log2; smaller merge tiles use less
                                 shared memory, so more CTAs fit per SM */
-    BS_OPT_MERGE_CONSUMER = 8 /* TMA merge consumers: 0 (default) each thread finds its own
+    BS_OPT_MERGE_CONSUMER = 8,/* TMA merge consumers: 0 (default) each thread finds its own
                                 merge-path split and merges its VT outputs sequentially;
                                 1 each warp merges a slice with a bitonic merger over
                                 registers, shuffles and a shared-memory transpose */
+    BS_OPT_HOST_DIRECT = 9   /* bs_sort_keys_host: 1 (default) reads and writes page-locked
+                                host buffers directly from the kernels; 0 always copies
+                                through device memory */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

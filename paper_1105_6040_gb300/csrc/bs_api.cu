@@ -170,6 +170,7 @@ struct bs_handle {
     int local_sort = BS_LOCAL_MERGE;
     int merge_tile_log2 = 0;  // 0: the sort tile
     int merge_consumer = 0;   // 0 per-thread sequential merge, 1 warp bitonic merger
+    int host_direct = 1;      // bs_sort_keys_host: address page-locked host buffers directly
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -321,17 +322,19 @@ inline unsigned blocks_for(int64_t work, int threads, int cap) {
 
 // The whole method for one call.  balanced: blocks are floor(i*n/p); else
 // user_off holds S+1 segment offsets (no cross-block rounds).
+// fin_k (nullable): where the decoded keys go instead of kout, which then
+// only serves as ping-pong buffer 0 (pinned host memory the GPU addresses).
 bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, void *vout, int64_t n,
                   bs_dtype kt, int vbytes, bool balanced, int64_t p, const int64_t *user_off,
                   int64_t S, int64_t max_len, cudaStream_t stream, const int64_t *src_off = nullptr,
-                  int64_t n_in = 0, bool oddeven = false) {
+                  int64_t n_in = 0, bool oddeven = false, void *fin_k = nullptr) {
     const int kw = key_width(kt);
     const int64_t blocks = balanced ? p : S;
     if (blocks > INT32_MAX) return BS_ERR_INVALID_ARG;
     // odd-even schedule: the sort runs on p padded blocks of cap keys each
     const int64_t slot_cap = oddeven ? (n + p - 1) / p : 0;
     const int64_t n_user = n;
-    const void *kout_user = kout;
+    const void *kout_user = fin_k ? fin_k : kout;
     if (oddeven) n = slot_cap * p;
     const WsLayout W = ws_layout(n, blocks, (size_t)kw, (size_t)vbytes);
     const size_t pad_bytes = oddeven ? (((size_t)n * kw + 255) & ~size_t(255)) : 0;
@@ -351,6 +354,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     g.wait_ns = h->wait_ns;
     g.withhold = h->withhold;
     g.R = balanced ? ceil_log2(p) : 0;
+    g.fin_k = oddeven ? nullptr : fin_k;  // the odd-even form decodes in its compaction
 
     Launcher L{stream, h, h->sms, launch_begin, launch_end};
     int codec = key_codec(kt);
@@ -430,7 +434,8 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.ntiles_ub = ub;
     a.ntiles_total = tprefix + blocks;
     a.split = (int64_t *)(ws + W.split);
-    const uintptr_t al = (uintptr_t)kout | (uintptr_t)a.k1 | (uintptr_t)vout | (uintptr_t)a.v1;
+    const uintptr_t al = (uintptr_t)kout | (uintptr_t)a.k1 | (uintptr_t)vout | (uintptr_t)a.v1 |
+                         (uintptr_t)g.fin_k;
     a.merge_impl = (al & 15) ? MERGE_SIMPLE : h->merge_impl;
     a.merge_vt = h->merge_vt;
     a.oddeven_rounds = oddeven ? (int)p : 0;
@@ -669,6 +674,17 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
+// Device address of host memory the GPU can access directly (page-locked
+// or registered, mapped into the unified address space), else nullptr.
+static void *host_device_ptr(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
                             int64_t p) {
     if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
@@ -692,12 +708,25 @@ bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t
         h->hb_bytes = bytes;
     }
     cudaStream_t s = h->own_stream;
-    if (cudaMemcpyAsync(h->hb, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return BS_ERR_CUDA;
-    bs_status st = bs_sort_keys(h, h->hb, h->hb, n, kt, p, (void *)s);
-    if (st != BS_OK) return st;
-    if (cudaMemcpyAsync(h_out, h->hb, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return BS_ERR_CUDA;
+    void *din = h->host_direct ? host_device_ptr(h_in) : nullptr;
+    void *dout = h->host_direct ? host_device_ptr(h_out) : nullptr;
+    if (din && dout) {
+        // the sort phase reads h_in and the last pass writes h_out across the
+        // host link; every other pass stays in HBM (hb and the workspace)
+        if (p == 0) p = 1;
+        if (p > n) p = n;
+        const bool oe = h->schedule == BS_SCHEDULE_ODDEVEN && p >= 2;
+        bs_status st = do_sort(h, din, h->hb, nullptr, nullptr, n, kt, 0, true, p, nullptr, p, 0, s,
+                               nullptr, 0, oe, dout);
+        if (st != BS_OK) return st;
+    } else {
+        if (cudaMemcpyAsync(h->hb, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return BS_ERR_CUDA;
+        bs_status st = bs_sort_keys(h, h->hb, h->hb, n, kt, p, (void *)s);
+        if (st != BS_OK) return st;
+        if (cudaMemcpyAsync(h_out, h->hb, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return BS_ERR_CUDA;
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) return BS_ERR_CUDA;
     return BS_OK;
 }
@@ -817,6 +846,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
     case BS_OPT_MERGE_TILE_LOG2:
         if (value != 0 && (value < 11 || value > 13)) return BS_ERR_INVALID_ARG;
         h->merge_tile_log2 = (int)value;
+        return BS_OK;
+    case BS_OPT_HOST_DIRECT:
+        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        h->host_direct = (int)value;
         return BS_OK;
     case BS_OPT_MERGE_CONSUMER:
         if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;

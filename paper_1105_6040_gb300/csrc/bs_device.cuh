@@ -98,7 +98,16 @@ struct Geo {
     int64_t n_in;                  // length of the input array when src_off is set
     uint64_t wait_ns;              // limit of every bounded wait (0: the default)
     int withhold;                  // test hook: CTA 0's producer withholds its first stage
+    void *fin_k, *fin_v;           // final (decoded) outputs go here when set, else to
+                                   // buffer 0 (e.g. pinned host memory the GPU addresses)
 };
+
+// Destination of a pass's output: the final buffers when this is the last
+// pass of its run and they are set, else ping-pong buffer `parity`.
+template <class T>
+__device__ __forceinline__ T *out_buf(bool fin, void *fin_buf, int parity, T *buf0, T *buf1) {
+    return (fin && fin_buf) ? static_cast<T *>(fin_buf) : (parity ? buf1 : buf0);
+}
 
 // kernel classes of the statistics counters (same order as the C ABI's)
 enum : int { CLS_TILE_SORT = 0, CLS_MERGE = 1, CLS_PARTITION = 2, CLS_SETUP = 3 };
@@ -421,8 +430,8 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
         const int L = seg_levels(shi - slo, g.logT);
         const int par = (L + g.R) & 1;
         const bool fin = (L + g.R) == 0;
-        K *dst_k = par ? buf_k1 : buf_k0;
-        V *dst_v = par ? buf_v1 : buf_v0;
+        K *dst_k = out_buf<K>(fin, g.fin_k, par, buf_k0, buf_k1);
+        V *dst_v = out_buf<V>(fin, g.fin_v, par, buf_v0, buf_v1);
         // where this tile's keys come from: in place, or (gathered segments)
         // from the segment's own offset in the input array, kept inside it
         int64_t ibase = base;
@@ -562,7 +571,7 @@ tile_bubble_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int 
             }
             __syncthreads();
         }
-        K *dst = ti.par ? buf_k1 : buf_k0;
+        K *dst = out_buf<K>(ti.fin, g.fin_k, ti.par, buf_k0, buf_k1);
         for (int pos = tid; pos < ti.cnt; pos += THREADS) {
             const K c = sk[pos];
             dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
@@ -685,7 +694,7 @@ tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int c
             }
         }
         __syncthreads();
-        K *dst = ti.par ? buf_k1 : buf_k0;
+        K *dst = out_buf<K>(ti.fin, g.fin_k, ti.par, buf_k0, buf_k1);
         for (int pos = tid; pos < ti.cnt; pos += THREADS) {
             const K c = sk[pos];
             dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
@@ -917,7 +926,8 @@ merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int cod
         const Slice q = tile_slice(p, split, t);
         cta_merge<K, V, THREADS, VT>(p.src ? buf_k1 : buf_k0, p.src ? buf_v1 : buf_v0, q.a_lo,
                                      (int)(q.a_hi - q.a_lo), q.b_lo, (int)(q.b_hi - q.b_lo),
-                                     p.dst ? buf_k1 : buf_k0, p.dst ? buf_v1 : buf_v0, p.x0, p.fin,
+                                     out_buf<K>(p.fin, g.fin_k, p.dst, buf_k0, buf_k1),
+                                     out_buf<V>(p.fin, g.fin_v, p.dst, buf_v0, buf_v1), p.x0, p.fin,
                                      codec, sk, sv);
         if (threadIdx.x == 0)
             atomicAdd(g.counters + CLS_MERGE,
@@ -1590,9 +1600,9 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
             K *sb = stage_k(s) + d.b_off;
             const int na = d.na, nb = d.nb, total_out = na + nb;
             unsigned char *ws = smem_raw + STAGES * LY::stage + (tid >> 5) * WS::bytes;
-            K *dk = (d.flags & 2) ? buf_k1 : buf_k0;
-            V *dv = (d.flags & 2) ? buf_v1 : buf_v0;
             const bool fin = (d.flags & 4) != 0;
+            K *dk = out_buf<K>(fin, g.fin_k, (d.flags >> 1) & 1, buf_k0, buf_k1);
+            V *dv = out_buf<V>(fin, g.fin_v, (d.flags >> 1) & 1, buf_v0, buf_v1);
             if constexpr (WARPMERGE)
                 warp_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv,
                                           d.o_lo, fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),

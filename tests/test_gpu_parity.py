@@ -253,6 +253,43 @@ def test_host_buffer_entry_point(sorter):
     assert np.array_equal(out.numpy(), oracle.sort(x, p=2)[0])
 
 
+@pytest.mark.parametrize("direct", [1, 0])
+@pytest.mark.parametrize("case", ["one_tile", "p2", "p8_float", "uint64_p3", "oddeven_p5", "in_place",
+                                  "pageable"])
+def test_host_entry_direct_and_copy(direct, case):
+    """bs_sort_keys_host gives the oracle's output whether the kernels address
+    the page-locked host buffers directly or copy through device memory."""
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    try:
+        abi.bs_set_option(s.h, "host_direct", direct)
+        p, dt = 2, "int32"
+        if case == "one_tile":
+            x, p = W.uniform_int32(3000, 90), 1
+        elif case == "p2":
+            x = W.uniform_int32(300001, 91)
+        elif case == "p8_float":
+            x, p = W.normal_float32_edges(1 << 20, 92), 8
+        elif case == "uint64_p3":
+            x, p = W.uniform_uint64(200003, 93), 3
+        elif case == "oddeven_p5":
+            abi.bs_set_option(s.h, "merge_schedule", 1)
+            x, p = W.uniform_int32(100003, 94), 5
+        else:
+            x = W.dup16_int32(250000, 95)
+        want = oracle.sort(x, p=p)[0]
+        if case == "pageable":
+            h_in, h_out = torch.from_numpy(x.copy()), torch.empty(x.size, dtype=torch.from_numpy(x).dtype)
+        else:
+            h_in = torch.from_numpy(x.copy()).pin_memory()
+            h_out = h_in if case == "in_place" else torch.empty_like(h_in).pin_memory()
+        s.sort_keys_host(h_in, h_out, p=p)
+        assert np.array_equal(_bits(h_out.numpy()), _bits(want))
+    finally:
+        s.close()
+
+
 def test_invalid_args(sorter):
     from paper_1105_6040_gb300 import abi
     t = torch.zeros(10, dtype=torch.int32, device="cuda")
