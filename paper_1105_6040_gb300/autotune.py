@@ -1,11 +1,12 @@
 """Autotuner for the sort's launch shapes.
 
-The tunable knobs are the tile size T = 2^tile_log2 keys (128, 256 or 512
-threads per CTA, 16 keys per thread; T is both the sort-phase tile and the
-merge-pass output tile), the merge-pass kernel (the TMA pipeline or the
-plain shared-memory one) and, for the TMA pipeline, the keys per consumer
-thread (16, or 8 with twice the consumer warps).  Results never depend on
-them; speed does.
+The tunable knobs are the sort-phase tile size T = 2^tile_log2 keys (128,
+256 or 512 threads per CTA, 16 keys per thread), the merge-pass output tile
+(the sort tile, or 4096 keys under 8192-key sort tiles), the merge-pass
+kernel (the TMA pipeline or the plain shared-memory one) and, for the TMA
+pipeline, the keys per consumer thread (the library's choice by item size:
+32 for 32-bit keys alone, else 16; or 16 or 8 explicitly).  Results never
+depend on them; speed does.
 
 ``tune(...)`` times every candidate on the caller's own inputs with CUDA
 events (after a warm-up run), keeps the fastest, and remembers it in a JSON
@@ -26,9 +27,10 @@ from . import abi
 
 TILE_LOG2 = (11, 12, 13)
 MERGE_KERNELS = ("auto", "simple")
-# (tile_log2, merge_kernel, merge_vt); 8 keys per consumer needs tiles <= 4096
-CANDIDATES = [(t, "auto", 16) for t in TILE_LOG2] + [(t, "auto", 8) for t in (11, 12)] + \
-    [(t, "simple", 16) for t in TILE_LOG2]
+# (tile_log2, merge_tile_log2 (0: the sort tile), merge_kernel, merge_vt (0: by item size))
+CANDIDATES = [(t, 0, "auto", 0) for t in TILE_LOG2] + [(13, 12, "auto", 0)] + \
+    [(t, 0, "auto", 16) for t in (11, 12)] + [(t, 0, "auto", 8) for t in (11, 12)] + \
+    [(t, 0, "simple", 16) for t in (11, 12)]
 
 _lock = threading.Lock()
 
@@ -83,8 +85,9 @@ def lookup(key: str):
 
 def apply(sorter: abi.Sorter, cfg: dict) -> None:
     abi.bs_set_option(sorter.h, "tile_log2", cfg["tile_log2"])
+    abi.bs_set_option(sorter.h, "merge_tile_log2", cfg.get("merge_tile_log2", 0))
     abi.bs_set_option(sorter.h, "merge_kernel", cfg["merge_kernel"])
-    abi.bs_set_option(sorter.h, "merge_vt", cfg.get("merge_vt", 16))
+    abi.bs_set_option(sorter.h, "merge_vt", cfg.get("merge_vt", 0))
 
 
 def _time_call(fn, repeats: int) -> float:
@@ -104,7 +107,7 @@ def _time_call(fn, repeats: int) -> float:
 
 def tune(sorter: abi.Sorter, kind: str, keys, vals=None, offsets=None, p: int = 1,
          max_seg_len: int = 0, repeats: int = 2, force: bool = False) -> dict:
-    """Pick (tile_log2, merge_kernel) for this workload class, apply it to
+    """Pick the launch shape for this workload class, apply it to
     `sorter` and return it.  kind: "keys", "pairs" or "segmented"."""
     import torch
     key = workload_key(kind, keys, vals, offsets, max_seg_len)
@@ -125,13 +128,13 @@ def tune(sorter: abi.Sorter, kind: str, keys, vals=None, offsets=None, p: int = 
             sorter.sort_segmented(keys, offsets, vals, kout=kout, vout=vout, max_seg_len=max_seg_len)
 
     timings = {}
-    for tile, merge, vt in CANDIDATES:
-        apply(sorter, {"tile_log2": tile, "merge_kernel": merge, "merge_vt": vt})
-        timings[f"{tile}/{merge}/{vt}"] = _time_call(run, repeats)
+    for tile, mtile, merge, vt in CANDIDATES:
+        apply(sorter, {"tile_log2": tile, "merge_tile_log2": mtile, "merge_kernel": merge, "merge_vt": vt})
+        timings[f"{tile}/{mtile}/{merge}/{vt}"] = _time_call(run, repeats)
     sorter.sync()
     best = min(timings, key=timings.get)
-    tile, merge, vt = best.split("/")
-    cfg = {"tile_log2": int(tile), "merge_kernel": merge, "merge_vt": int(vt),
+    tile, mtile, merge, vt = best.split("/")
+    cfg = {"tile_log2": int(tile), "merge_tile_log2": int(mtile), "merge_kernel": merge, "merge_vt": int(vt),
            "ms": timings[best], "timings_ms": timings}
     with _lock:
         cache = _load()
