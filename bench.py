@@ -656,6 +656,7 @@ def run_psweep(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    args.tile_log2, args.merge_tile_log2 = 12, 0  # the 4096-key tile every row uses (for config())
     n = 1 << args.log2n
     x = torch.from_numpy(make_keys(args, 0)).cuda()
     out = torch.empty_like(x)
@@ -701,6 +702,7 @@ def run_localsort(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    args.tile_log2, args.merge_tile_log2 = 12, 0  # the 4096-key tile every row uses (for config())
     n = 1 << args.log2n
     x = torch.from_numpy(make_keys(args, 0)).cuda()
     out = torch.empty_like(x)

@@ -639,13 +639,21 @@ tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int c
             else if (ti.cnt > 1) small[nsmall++] = make_int2(0, ti.cnt);
         }
         __syncthreads();
-        while (top > 0) {
+        for (;;) {
+            // thread 0 pops the next segment (or -1 when none is left) and
+            // publishes it; every thread reads it after the barrier, and
+            // thread 0 writes it again only after the body's last barrier
             if (tid == 0) {
-                const int2 sg = stack[--top];
-                seg_lo = sg.x;
-                seg_hi = sg.y;
+                if (top > 0) {
+                    const int2 sg = stack[--top];
+                    seg_lo = sg.x;
+                    seg_hi = sg.y;
+                } else {
+                    seg_lo = -1;
+                }
             }
             __syncthreads();
+            if (seg_lo < 0) break;
             const int lo = seg_lo, hi = seg_hi, len = hi - lo, mid = lo + len / 2;
             const K pivot = sk[mid];
             // this thread's chunk of the segment
@@ -673,9 +681,11 @@ tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int c
             if (tid == 0) {
                 const int2 sides[2] = {make_int2(lo, lo + tl), make_int2(lo + tl + 1, hi)};
                 for (int q = 0; q < 2; ++q) {
+                    // the pending segments are disjoint, so neither list can
+                    // overflow; the bounds are checked all the same
                     const int sl = sides[q].y - sides[q].x;
-                    if (sl > QS_SMALL) stack[top++] = sides[q];
-                    else if (sl > 1) small[nsmall++] = sides[q];
+                    if (sl > QS_SMALL && top < MAXSTACK) stack[top++] = sides[q];
+                    else if (sl > 1 && nsmall < T) small[nsmall++] = sides[q];
                 }
             }
             __syncthreads();

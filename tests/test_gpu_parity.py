@@ -496,6 +496,24 @@ def test_oddeven_schedule_matches_oracle(n, p):
 
 # ------------------------------------------------------------------ local sorts of Figs. 2 and 4
 
+@pytest.mark.parametrize("local", ["quick", "bubble"])
+def test_local_sort_many_tiles_per_cta(local):
+    """Thousands of tiles, so every CTA of the persistent tile-sort grid runs
+    many tiles back to back (quick sort's segment stack is shared state
+    between tiles and rounds)."""
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    s = Sorter(0)
+    try:
+        abi.bs_set_option(s.h, "local_sort", local)
+        n = (1 << 22) if local == "quick" else (1 << 20)
+        for x in (W.uniform_int32(n, 97), W.dup16_int32(n, 98)):
+            got = gpu_keys(s, x, 2)
+            assert np.array_equal(got, oracle.sort(x, p=2)[0]), (local, x[:4])
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("local", ["bubble", "quick"])
 def test_local_sort_variants_match_oracle(local):
     from paper_1105_6040_gb300 import abi
