@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--seg-hi-log2", type=int, default=17)
     ap.add_argument("--per-array-rounds", type=int, default=2)
     ap.add_argument("--merge-vt", type=int, default=0, choices=[0, 8, 16, 32])
-    ap.add_argument("--merge-tile-log2", type=int, default=12, choices=[0, 11, 12, 13])
+    ap.add_argument("--merge-tile-log2", type=int, default=0, choices=[0, 11, 12, 13],
+                    help="merge-pass tile 2^k keys (0: the sort tile)")
     ap.add_argument("--merge-consumer", type=int, default=0, choices=[0, 1])
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
@@ -68,8 +69,7 @@ def parse_args():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
     ap.add_argument("--tile-log2", type=int, default=13,
-                    help="sort-phase tile 2^k keys (the bench default: 8192-key sort tiles, "
-                         "merged in 4096-key merge tiles)")
+                    help="sort-phase tile 2^k keys (the bench default: 8192-key sort and merge tiles)")
     ap.add_argument("--merge", choices=["auto", "simple", "tma"], default="auto",
                     help="merge-pass kernel (auto: TMA pipeline where it fits)")
     ap.add_argument("--e2e-steps", type=int, default=20)
