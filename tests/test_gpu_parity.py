@@ -255,7 +255,7 @@ def test_host_buffer_entry_point(sorter):
 
 @pytest.mark.parametrize("direct", [1, 0])
 @pytest.mark.parametrize("case", ["one_tile", "p2", "p8_float", "uint64_p3", "oddeven_p5", "in_place",
-                                  "pageable"])
+                                  "pageable", "large_2e25", "large_float_in_place"])
 def test_host_entry_direct_and_copy(direct, case):
     """bs_sort_keys_host gives the oracle's output whether the kernels address
     the page-locked host buffers directly or copy through device memory."""
@@ -276,6 +276,10 @@ def test_host_entry_direct_and_copy(direct, case):
         elif case == "oddeven_p5":
             abi.bs_set_option(s.h, "merge_schedule", 1)
             x, p = W.uniform_int32(100003, 94), 5
+        elif case == "large_2e25":  # many tiles, ragged blocks
+            x, p = W.uniform_int32((1 << 25) + 12345, 96), 3
+        elif case == "large_float_in_place":
+            x, p = W.normal_float32_edges((1 << 26) + 7, 97), 2
         else:
             x = W.dup16_int32(250000, 95)
         want = oracle.sort(x, p=p)[0]
@@ -283,7 +287,7 @@ def test_host_entry_direct_and_copy(direct, case):
             h_in, h_out = torch.from_numpy(x.copy()), torch.empty(x.size, dtype=torch.from_numpy(x).dtype)
         else:
             h_in = torch.from_numpy(x.copy()).pin_memory()
-            h_out = h_in if case == "in_place" else torch.empty_like(h_in).pin_memory()
+            h_out = h_in if case.endswith("in_place") else torch.empty_like(h_in).pin_memory()
         s.sort_keys_host(h_in, h_out, p=p)
         assert np.array_equal(_bits(h_out.numpy()), _bits(want))
     finally:
