@@ -214,16 +214,30 @@ template <int N> struct OddEvenNet {
     }
 };
 
+// Applies comparator C and the ones after it, one template instance each,
+// so every register index is a compile-time constant (no local memory).
+template <int N, int C> struct OddEvenApply {
+    static constexpr OddEvenNet<N> net{};
+    template <class K> static __device__ __forceinline__ void keys(K (&k)[N]) {
+        if constexpr (C < net.n) {
+            cas_keys(k[net.a[C]], k[net.b[C]]);
+            OddEvenApply<N, C + 1>::keys(k);
+        }
+    }
+    template <class K> static __device__ __forceinline__ void pairs(K (&k)[N], uint32_t (&x)[N]) {
+        if constexpr (C < net.n) {
+            cas_pairs(k[net.a[C]], x[net.a[C]], k[net.b[C]], x[net.b[C]]);
+            OddEvenApply<N, C + 1>::pairs(k, x);
+        }
+    }
+};
+
 template <int N, class K> __device__ __forceinline__ void reg_sort_keys(K (&k)[N]) {
-    constexpr OddEvenNet<N> net{};
-#pragma unroll
-    for (int c = 0; c < net.n; ++c) cas_keys(k[net.a[c]], k[net.b[c]]);
+    OddEvenApply<N, 0>::keys(k);
 }
 
 template <int N, class K> __device__ __forceinline__ void reg_sort_pairs(K (&k)[N], uint32_t (&x)[N]) {
-    constexpr OddEvenNet<N> net{};
-#pragma unroll
-    for (int c = 0; c < net.n; ++c) cas_pairs(k[net.a[c]], x[net.a[c]], k[net.b[c]], x[net.b[c]]);
+    OddEvenApply<N, 0>::pairs(k, x);
 }
 
 // Ascending bitonic merge of a bitonic sequence held in N registers.
@@ -393,13 +407,13 @@ template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes
 // Merge rounds of the keys-only tile sort done with register shuffles
 // inside a warp before the shared-memory rounds take over.
 #ifndef TILE_SHUFFLE_ROUNDS
-#define TILE_SHUFFLE_ROUNDS 4
+#define TILE_SHUFFLE_ROUNDS 5
 #endif
 
 // Tile sort (the sort phase of Fig. 1 at CTA scale).  Tile t covers
 // keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
-// KPT keys in registers; keys-only tiles then merge pairs of lists with
-// TILE_SHUFFLE_ROUNDS warp-shuffle rounds, and the remaining rounds merge
+// KPT keys in registers; keys-only tiles then merge pairs of lists with up
+// to TILE_SHUFFLE_ROUNDS warp-shuffle rounds, and the remaining rounds merge
 // through shared memory (merge-path split + sequential merge of KPT
 // outputs per thread); rounds whose lists live inside one warp synchronise
 // only that warp.  Pairs sort

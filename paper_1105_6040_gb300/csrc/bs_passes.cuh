@@ -264,7 +264,17 @@ bs_status oddeven_compact_t(const void *in, void *out, int64_t n, int codec, Lau
 }
 
 // Dispatch on the value width and the sort tile shape (T = 2^logT = THREADS*16).
+// Sort-phase shapes (threads per CTA, keys per thread) by tile size: keys
+// alone sort 32 per thread (a 191-comparator register network, then five
+// warp-shuffle rounds reach 1024-key lists), pairs 16 per thread.
 template <class K, class V> bs_status run_passes_v(const PassArgs &a, Launcher &L) {
+    if constexpr (!HasVal<V>::value) {
+        switch (a.g.logT) {
+        case 12: return run_passes_t<K, V, 128, 32>(a, L);
+        case 13: return run_passes_t<K, V, 256, 32>(a, L);
+        default: break;
+        }
+    }
     switch (a.g.logT) {
     case 11: return run_passes_t<K, V, 128, 16>(a, L);
     case 12: return run_passes_t<K, V, 256, 16>(a, L);
