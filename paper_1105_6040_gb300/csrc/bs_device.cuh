@@ -6,15 +6,17 @@
 //   sort phase (Fig. 1): every block is cut into tiles of T keys
 //     aligned to the block start; one CTA sorts one tile in registers and
 //     shared memory (tile_sort_kernel), then merge passes in HBM join the
-//     sorted tiles of each block pairwise (seg_merge_kernel) until the block
+//     sorted tiles of each block pairwise (in-block levels) until the block
 //     is one sorted run.
-//   merge phase (Fig. 1): pairs of sorted blocks are merged,
-//     round after round (xblock_merge_kernel), until one run remains.
-// Every merge pass splits its output into tiles of T keys; the start of each
+//   merge phase (Fig. 1): pairs of sorted blocks are merged, round after
+//     round (cross-block levels), until one run remains.
+// Every merge pass splits its output into merge tiles; the start of each
 // output tile inside its pair of runs is found by a merge-path search
-// (Odeh, Green, Mwassi, Shmueli, Birk: "Merge Path", IPDPSW 2012), so each
-// CTA merges an independent slice.  Ties go to the left run, which makes all
-// merges stable.
+// (Odeh, Green, Mwassi, Shmueli, Birk: "Merge Path", IPDPSW 2012:
+// partition_kernel), so each CTA merges an independent slice, staged into
+// shared memory by TMA bulk copies (merge_tma_kernel; merge_kernel for
+// unaligned buffers).  Ties go to the left run, which makes all merges
+// stable.
 //
 // Keys travel as order-preserving unsigned codes (encoded when the tile sort
 // loads them, decoded by the pass that writes the final output), so every
