@@ -373,28 +373,28 @@ __device__ __forceinline__ void seq_merge_keys(const K *sk, int a0, int b0, int 
     }
 }
 
-// The same for pairs, ordered by (code, original position) as every pair
-// network here is; oi[] receives the positions.
+// The same for pairs whose lists cover consecutive ranges of original
+// positions (the left list's first): the left item on a tie is the stable
+// order, so only codes are compared; each output's staging index is kept
+// and its position fetched after the loop (independent loads).
 template <class K, int KPT>
-__device__ __forceinline__ void seq_merge_pairs(const K *sk, const uint32_t *sx, int a0, int b0, int m, int i,
+__device__ __forceinline__ void seq_merge_carry(const K *sk, const uint32_t *sx, int a0, int b0, int m, int i,
                                                 int j, K (&out)[KPT], uint32_t (&oi)[KPT]) {
     K a = sk[spad<K>(a0 + i)], b = sk[spad<K>(b0 + j)];
-    uint32_t xa = sx[spad<uint32_t>(a0 + i)], xb = sx[spad<uint32_t>(b0 + j)];
+    int from[KPT];
 #pragma unroll
     for (int u = 0; u < KPT; ++u) {
-        const bool tb = i >= m || (j < m && ki_less(b, xb, a, xa));
+        const bool tb = i >= m || (j < m && b < a);  // take B's head
         out[u] = tb ? b : a;
-        oi[u] = tb ? xb : xa;
+        from[u] = tb ? b0 + j : a0 + i;
         i += tb ? 0 : 1;
         j += tb ? 1 : 0;
-        const int at = tb ? b0 + j : a0 + i;
-        const K nxt = sk[spad<K>(at)];
-        const uint32_t nx = sx[spad<uint32_t>(at)];
+        const K nxt = sk[spad<K>(tb ? b0 + j : a0 + i)];
         a = tb ? a : nxt;
-        xa = tb ? xa : nx;
         b = tb ? nxt : b;
-        xb = tb ? nx : xb;
     }
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) oi[u] = sx[spad<uint32_t>(from[u])];
 }
 
 // ---------------------------------------------------------------- tile sort
@@ -462,17 +462,34 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
         // for pairs, positions past every real one)
         K k[KPT];
         uint32_t x[KPT];
+        if constexpr (HV) {
+            // pairs: thread t takes positions KPT*t .. KPT*t + KPT-1 (through
+            // shared memory), so every list the rounds merge covers one range
+            // of positions and the left list's items all come first: taking
+            // the left item on a tie is then the stable order, and only the
+            // register network compares (code, position)
 #pragma unroll
-        for (int u = 0; u < KPT; ++u) {
-            const int pos = tid + u * THREADS;
-            k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
-            if constexpr (HV) {
-                x[u] = (uint32_t)pos;
+            for (int u = 0; u < KPT; ++u) {
+                const int pos = tid + u * THREADS;
+                sk[spad<K>(pos)] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
                 if (pos < lcnt) sv[spad<V>(pos)] = in_v[ibase + pos];
             }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                k[u] = sk[spad<K>(tid * KPT + u)];
+                x[u] = (uint32_t)(tid * KPT + u);
+            }
+            __syncthreads();  // the first round overwrites sk
+            reg_sort_pairs<KPT>(k, x);
+        } else {
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int pos = tid + u * THREADS;
+                k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
+            }
+            reg_sort_keys<KPT>(k);
         }
-        if constexpr (HV) reg_sort_pairs<KPT>(k, x);
-        else reg_sort_keys<KPT>(k);
 
         int r0 = 0;
         if constexpr (!HV) {
@@ -497,10 +514,9 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
             const int diag = (tid & ((2 << r) - 1)) * KPT;
             if constexpr (HV) {
                 const int i = merge_path_pred<int>(m, m, diag, [&](int ia, int ib) {
-                    return ki_less(sk[spad<K>(b0 + ib)], sx[spad<uint32_t>(b0 + ib)],
-                                   sk[spad<K>(a0 + ia)], sx[spad<uint32_t>(a0 + ia)]);
+                    return sk[spad<K>(b0 + ib)] < sk[spad<K>(a0 + ia)];
                 });
-                seq_merge_pairs<K, KPT>(sk, sx, a0, b0, m, i, diag - i, k, x);
+                seq_merge_carry<K, KPT>(sk, sx, a0, b0, m, i, diag - i, k, x);
             } else {
                 const int i = merge_path_pred<int>(m, m, diag, [&](int ia, int ib) {
                     return sk[spad<K>(b0 + ib)] < sk[spad<K>(a0 + ia)];
