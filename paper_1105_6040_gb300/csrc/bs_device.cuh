@@ -114,6 +114,11 @@ __device__ __forceinline__ T *out_buf(bool fin, void *fin_buf, int parity, T *bu
 // kernel classes of the statistics counters (same order as the C ABI's)
 enum : int { CLS_TILE_SORT = 0, CLS_MERGE = 1, CLS_PARTITION = 2, CLS_SETUP = 3 };
 
+// Kernels launched with programmatic stream serialization may start while
+// the previous kernel on their stream finishes: they call this before
+// touching anything it wrote (a no-op for a plain launch).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int64_t clamp64(int64_t x, int64_t lo, int64_t hi) {
     return x < lo ? lo : (x > hi ? hi : x);
 }
@@ -918,6 +923,7 @@ __device__ __forceinline__ int64_t level_tiles(const Geo &g, const Level &L,
 template <class K>
 __global__ void partition_kernel(Geo g, Level L, const K *buf0, const K *buf1, int64_t *split,
                                  const int64_t *__restrict__ ntiles_total) {
+    griddep_wait();
     const int64_t total = level_tiles(g, L, ntiles_total);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -961,6 +967,7 @@ merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int cod
     extern __shared__ __align__(128) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
     V *sv = reinterpret_cast<V *>(smem_raw + smem_val_offset<K>(TT));
+    griddep_wait();
     const int64_t total = level_tiles(g, L, ntiles_total);
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
         const TilePair p = tile_pair(g, L, t);
@@ -1554,6 +1561,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
         mbar_fence_init();
     }
     __syncthreads();
+    griddep_wait();  // the splits and the runs come from the kernels before
 
     const int64_t total = level_tiles(g, L, ntiles_total);
     const int64_t n = g.n;

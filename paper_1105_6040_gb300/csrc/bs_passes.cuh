@@ -30,6 +30,26 @@ template <class Kern> static bool allow_smem(Kern kern, size_t smem) {
            cudaSuccess;
 }
 
+// Launches `kern` with programmatic stream serialization: its CTAs may be
+// scheduled, and run up to their griddepcontrol.wait, while the kernel before
+// it on the stream drains, which hides most of the gap between two kernels.
+// Only kernels that wait before touching global memory are launched so.
+template <class... Params, class... Args>
+static cudaError_t launch_overlapped(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
+                                     cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, (Params)args...);
+}
+
 static inline int64_t grid_for(int64_t work, int64_t resident) {
     int64_t g = work < resident ? work : resident;
     return g < 1 ? 1 : g;
@@ -60,8 +80,9 @@ int launch_merge_tma(const PassArgs &a, Launcher &L, const Level &lvl, int64_t t
     if (occ_mt[ci].load() <= 0) return 0;
     if (a.merge_impl == MERGE_AUTO && msmem > TMA_SMEM_AUTO_LIMIT) return 0;
     const Geo &g = a.g;
-    mt<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt[ci]), MT + 32, msmem, L.stream>>>(
-        g, lvl, (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, a.split, a.ntiles_total);
+    launch_overlapped(mt, (unsigned)grid_for(tiles, (int64_t)L.sms * occ_mt[ci]), MT + 32, msmem, L.stream, g,
+                      lvl, (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, (const int64_t *)a.split,
+                      a.ntiles_total);
     return 1;
 }
 
@@ -76,8 +97,9 @@ bool launch_merge_plain(const PassArgs &a, Launcher &L, const Level &lvl, int64_
         occ_mk.store(resident_ctas(mk, MT, smem));
     }
     const Geo &g = a.g;
-    mk<<<(unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream>>>(
-        g, lvl, (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, a.split, a.ntiles_total);
+    launch_overlapped(mk, (unsigned)grid_for(tiles, (int64_t)L.sms * occ_mk), MT, smem, L.stream, g, lvl,
+                      (K *)a.k0, (K *)a.k1, (V *)a.v0, (V *)a.v1, a.codec, (const int64_t *)a.split,
+                      a.ntiles_total);
     return true;
 }
 
@@ -114,9 +136,10 @@ template <class K, class V>
 bool merge_pass_any(const PassArgs &a, Launcher &L, const Level &lvl, int64_t tiles) {
     const Geo &g = a.g;
     L.begin(L.owner, CLS_PARTITION, L.stream);
-    partition_kernel<K><<<(unsigned)grid_for((tiles + PART_THREADS - 1) / PART_THREADS, (int64_t)L.sms * 8),
-                          PART_THREADS, 0, L.stream>>>(g, lvl, (const K *)a.k0, (const K *)a.k1, a.split,
-                                                       a.ntiles_total);
+    launch_overlapped(partition_kernel<K>,
+                      (unsigned)grid_for((tiles + PART_THREADS - 1) / PART_THREADS, (int64_t)L.sms * 8),
+                      PART_THREADS, 0, L.stream, g, lvl, (const K *)a.k0, (const K *)a.k1, a.split,
+                      a.ntiles_total);
     if (!L.end(L.owner, CLS_PARTITION, L.stream)) return false;
     L.begin(L.owner, CLS_MERGE, L.stream);
     int done = 0;
