@@ -29,6 +29,7 @@ using namespace bs;
 
 // Scatter bounds b_i = floor(i*n/p), i = 0..p (Fig. 1, scatter phase).
 __global__ void balanced_offsets_kernel(int64_t *off, int64_t n, int64_t p) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= p;
          i += (int64_t)gridDim.x * blockDim.x) {
         unsigned __int128 v = (unsigned __int128)(uint64_t)i * (uint64_t)n;
@@ -40,6 +41,7 @@ __global__ void balanced_offsets_kernel(int64_t *off, int64_t n, int64_t p) {
 // bound is given) hold no segment longer than max_len.
 __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n, int64_t max_len,
                                         int *err) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = off[i], hi = off[i + 1];
@@ -54,6 +56,7 @@ __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n
 // array of n_in items.
 __global__ void validate_gather_kernel(const int64_t *off, const int64_t *src_off, int64_t S,
                                        int64_t n_in, int *err) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t len = off[i + 1] - off[i], so = src_off[i];
@@ -73,6 +76,7 @@ __global__ void __launch_bounds__(SCAN_TH)
 tile_scan_block_kernel(const int64_t *off, int64_t S, int64_t n, int logT, int64_t *tprefix,
                        int64_t *bsum) {
     __shared__ int64_t warp_tot[SCAN_TH / 32];
+    griddep_wait();
     const int64_t base = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x * (int64_t)SCAN_IT;
     int64_t v[SCAN_IT];
     int64_t run = 0;
@@ -105,6 +109,7 @@ tile_scan_block_kernel(const int64_t *off, int64_t S, int64_t n, int logT, int64
 
 // Exclusive scan of the block totals in place (one CTA, chunked with carry).
 __global__ void tile_scan_top_kernel(int64_t *bsum, int64_t nb) {
+    griddep_wait();
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -131,6 +136,7 @@ __global__ void tile_scan_top_kernel(int64_t *bsum, int64_t nb) {
 }
 
 __global__ void tile_scan_add_kernel(int64_t *tprefix, const int64_t *bsum, int64_t S) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
          i += (int64_t)gridDim.x * blockDim.x)
         tprefix[i + 1] += bsum[i / SCAN_BLOCK];
@@ -138,6 +144,7 @@ __global__ void tile_scan_add_kernel(int64_t *tprefix, const int64_t *bsum, int6
 
 // tseg[t] = the segment owning tile t (t < total tiles).
 __global__ void tile_map_kernel(const int64_t *tprefix, int64_t S, int32_t *tseg, int64_t ub) {
+    griddep_wait();
     const int64_t total = tprefix[S];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ub && t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -373,19 +380,19 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     if (balanced) {
         int64_t *off = (int64_t *)(ws + W.off);
         launch_begin(h, CLS_SETUP, stream);
-        balanced_offsets_kernel<<<blocks_for(p + 1, 256, cap), 256, 0, stream>>>(off, n, p);
+        launch_overlapped(balanced_offsets_kernel, blocks_for(p + 1, 256, cap), 256, 0, stream, off, n, p);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
         g.off = off;
     } else {
         launch_begin(h, CLS_SETUP, stream);
-        validate_offsets_kernel<<<blocks_for(S, 256, cap), 256, 0, stream>>>(user_off, S, n, max_len,
-                                                                            h->d_err);
+        launch_overlapped(validate_offsets_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off, S, n,
+                          max_len, h->d_err);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
         g.off = user_off;
         if (src_off) {
             launch_begin(h, CLS_SETUP, stream);
-            validate_gather_kernel<<<blocks_for(S, 256, cap), 256, 0, stream>>>(user_off, src_off, S,
-                                                                               n_in, h->d_err);
+            launch_overlapped(validate_gather_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off,
+                              src_off, S, n_in, h->d_err);
             if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
             g.src_off = src_off;
             g.n_in = n_in;
@@ -397,22 +404,24 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     int64_t *bsum = (int64_t *)(ws + W.bsum);
     const int64_t nsb = (blocks + SCAN_BLOCK - 1) / SCAN_BLOCK;
     launch_begin(h, CLS_SETUP, stream);
-    tile_scan_block_kernel<<<(unsigned)nsb, SCAN_TH, 0, stream>>>(g.off, blocks, n, g.logT, tprefix,
-                                                                  bsum);
+    launch_overlapped(tile_scan_block_kernel, (unsigned)nsb, SCAN_TH, 0, stream, g.off, blocks, n, g.logT,
+                      tprefix, bsum);
     if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     if (nsb > 1) {
         launch_begin(h, CLS_SETUP, stream);
-        tile_scan_top_kernel<<<1, 1024, 0, stream>>>(bsum, nsb);
+        launch_overlapped(tile_scan_top_kernel, 1, 1024, 0, stream, bsum, nsb);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
         launch_begin(h, CLS_SETUP, stream);
-        tile_scan_add_kernel<<<blocks_for(blocks, 256, cap), 256, 0, stream>>>(tprefix, bsum, blocks);
+        launch_overlapped(tile_scan_add_kernel, blocks_for(blocks, 256, cap), 256, 0, stream, tprefix, bsum,
+                          blocks);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     }
     const int64_t T = int64_t(1) << g.logT;
     const int64_t ub = (n + T - 1) / T + blocks;
     g.ntiles_ub = ub;
     launch_begin(h, CLS_SETUP, stream);
-    tile_map_kernel<<<blocks_for(ub, 256, cap), 256, 0, stream>>>(tprefix, blocks, (int32_t *)g.tseg, ub);
+    launch_overlapped(tile_map_kernel, blocks_for(ub, 256, cap), 256, 0, stream, tprefix, blocks,
+                      (int32_t *)g.tseg, ub);
     if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
 
     PassArgs a{};
@@ -556,8 +565,8 @@ bs_status bs_sort_segmented(bs_handle *h, const void *d_kin, void *d_kout, const
         // still check the offsets (all must be 0)
         h->last_stream = (cudaStream_t)stream;
         launch_begin(h, CLS_SETUP, (cudaStream_t)stream);
-        validate_offsets_kernel<<<blocks_for(S, 256, h->sms * 8), 256, 0, (cudaStream_t)stream>>>(
-            d_offsets, S, 0, 0, h->d_err);
+        launch_overlapped(validate_offsets_kernel, blocks_for(S, 256, h->sms * 8), 256, 0,
+                          (cudaStream_t)stream, d_offsets, S, 0, 0, h->d_err);
         return launch_end(h, CLS_SETUP, (cudaStream_t)stream) ? BS_OK : BS_ERR_CUDA;
     }
     return do_sort(h, d_kin, d_kout, has_v ? d_vin : nullptr, has_v ? d_vout : nullptr, n, kt,

@@ -434,6 +434,7 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
                  const int64_t *__restrict__ ntiles_total) {
     constexpr int T = THREADS * KPT;
     constexpr bool HV = HasVal<V>::value;
+    griddep_wait();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
     uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw + smem_val_offset<K>(T));
@@ -594,6 +595,7 @@ tile_bubble_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int 
     constexpr int T = THREADS * KPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     K *sk = reinterpret_cast<K *>(smem_raw);
+    griddep_wait();
     const int64_t total = min(*ntiles_total, g.ntiles_ub);
     const int tid = threadIdx.x;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -657,6 +659,7 @@ tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int c
     constexpr int T = THREADS * KPT;
     constexpr int MAXSTACK = T / QS_SMALL + 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    griddep_wait();
     K *sk = reinterpret_cast<K *>(smem_raw);
     K *tmp = sk + T;
     int2 *stack = reinterpret_cast<int2 *>(tmp + T);
@@ -989,6 +992,7 @@ merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int cod
 template <class K, class V>
 __global__ void encode_copy_kernel(const K *__restrict__ in_k, const V *__restrict__ in_v, K *out_k,
                                    V *out_v, int64_t n, int codec) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         out_k[i] = enc_code(in_k[i], codec);
@@ -1002,6 +1006,7 @@ __global__ void encode_copy_kernel(const K *__restrict__ in_k, const V *__restri
 template <class K>
 __global__ void pad_scatter_kernel(const K *__restrict__ in, K *out, int64_t n, int64_t p, int64_t cap,
                                    int codec) {
+    griddep_wait();
     const int64_t total = p * cap;
     for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < total;
          y += (int64_t)gridDim.x * blockDim.x) {
@@ -1015,6 +1020,7 @@ __global__ void pad_scatter_kernel(const K *__restrict__ in, K *out, int64_t n, 
 // Odd-even schedule, last step: the first n slots hold the sorted keys.
 template <class K>
 __global__ void decode_copy_kernel(const K *__restrict__ in, K *out, int64_t n, int codec) {
+    griddep_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = dec_code(in[i], codec);

@@ -8,6 +8,26 @@
 
 namespace bs {
 
+// Launches `kern` with programmatic stream serialization: its CTAs may be
+// scheduled, and run up to their griddepcontrol.wait, while the kernel before
+// it on the stream drains, which hides most of the gap between two kernels.
+// Only kernels that wait before touching global memory are launched so.
+template <class... Params, class... Args>
+inline cudaError_t launch_overlapped(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
+                                     cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, (Params)args...);
+}
+
 // Launch bookkeeping supplied by the C ABI layer: launch counting, optional
 // CUDA-event timing per launch, and error capture.
 struct Launcher {

@@ -170,13 +170,13 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
 
     // scatter bounds, tiles per block (p <= 1024 fits one scan block), tile map
     const unsigned pb = (unsigned)((p + 1 + 255) / 256);
-    balanced_offsets_kernel<<<pb, 256, 0, s>>>(off, n, p);
+    bs::launch_overlapped(balanced_offsets_kernel, pb, 256, 0, s, off, n, p);
     if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
-    tile_scan_block_kernel<<<1, SCAN_THREADS, 0, s>>>(off, p, n, LOGT, tprefix, bsum);
+    bs::launch_overlapped(tile_scan_block_kernel, 1, SCAN_THREADS, 0, s, off, p, n, LOGT, tprefix, bsum);
     if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
     unsigned mb = (unsigned)((ub + 255) / 256);
     if (mb > (unsigned)sms * 8) mb = (unsigned)sms * 8;
-    tile_map_kernel<<<mb, 256, 0, s>>>(tprefix, p, tseg, ub);
+    bs::launch_overlapped(tile_map_kernel, mb, 256, 0, s, tprefix, p, tseg, ub);
     if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
 
     bs::PassArgs a{};

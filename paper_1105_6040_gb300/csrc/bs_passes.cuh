@@ -30,26 +30,6 @@ template <class Kern> static bool allow_smem(Kern kern, size_t smem) {
            cudaSuccess;
 }
 
-// Launches `kern` with programmatic stream serialization: its CTAs may be
-// scheduled, and run up to their griddepcontrol.wait, while the kernel before
-// it on the stream drains, which hides most of the gap between two kernels.
-// Only kernels that wait before touching global memory are launched so.
-template <class... Params, class... Args>
-static cudaError_t launch_overlapped(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
-                                     cudaStream_t stream, Args... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, (Params)args...);
-}
-
 static inline int64_t grid_for(int64_t work, int64_t resident) {
     int64_t g = work < resident ? work : resident;
     return g < 1 ? 1 : g;
@@ -201,9 +181,9 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     if (a.merge_only) {
         // runs arrive sorted: encode them into the buffer the rounds start from
         L.begin(L.owner, CLS_SETUP, L.stream);
-        encode_copy_kernel<K, V><<<(unsigned)grid_for((g.n + 255) / 256, (int64_t)L.sms * 8), 256, 0,
-                                   L.stream>>>((const K *)a.in_k, (const V *)a.in_v,
-                                               (g.R & 1) ? k1 : k0, (g.R & 1) ? v1 : v0, g.n, a.codec);
+        launch_overlapped(encode_copy_kernel<K, V>, (unsigned)grid_for((g.n + 255) / 256, (int64_t)L.sms * 8),
+                          256, 0, L.stream, (const K *)a.in_k, (const V *)a.in_v, (g.R & 1) ? k1 : k0,
+                          (g.R & 1) ? v1 : v0, g.n, a.codec);
         if (!L.end(L.owner, CLS_SETUP, L.stream)) return BS_ERR_CUDA;
     } else if (!HasVal<V>::value && a.local_sort == 1) {
         // sort phase with Fig. 2's bubble sort (odd-even transposition per tile)
@@ -212,8 +192,8 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
         static std::atomic<int> occ_b{0};
         if (!occ_b.load()) occ_b.store(resident_ctas(kb, THREADS, sb));
         L.begin(L.owner, CLS_TILE_SORT, L.stream);
-        kb<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_b), THREADS, sb, L.stream>>>(
-            g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
+        launch_overlapped(kb, (unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_b), THREADS, sb, L.stream,
+                          g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     } else if (!HasVal<V>::value && a.local_sort == 2) {
         // sort phase with Fig. 4's quick sort (CTA partition per tile)
@@ -225,14 +205,15 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
             occ_q.store(resident_ctas(kq, THREADS, sq));
         }
         L.begin(L.owner, CLS_TILE_SORT, L.stream);
-        kq<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_q), THREADS, sq, L.stream>>>(
-            g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
+        launch_overlapped(kq, (unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_q), THREADS, sq, L.stream,
+                          g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     } else {
         // sort phase: every tile of every block
         L.begin(L.owner, CLS_TILE_SORT, L.stream);
-        ts<<<(unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem, L.stream>>>(
-            g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec, a.ntiles_total);
+        launch_overlapped(ts, (unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem,
+                          L.stream, g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec,
+                          a.ntiles_total);
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     }
 
@@ -273,16 +254,16 @@ template <class K>
 bs_status oddeven_scatter_t(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
                             Launcher &L) {
     L.begin(L.owner, CLS_SETUP, L.stream);
-    pad_scatter_kernel<K><<<(unsigned)grid_for((p * cap + 255) / 256, (int64_t)L.sms * 8), 256, 0,
-                            L.stream>>>((const K *)in, (K *)out, n, p, cap, codec);
+    launch_overlapped(pad_scatter_kernel<K>, (unsigned)grid_for((p * cap + 255) / 256, (int64_t)L.sms * 8),
+                      256, 0, L.stream, (const K *)in, (K *)out, n, p, cap, codec);
     return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
 }
 
 template <class K>
 bs_status oddeven_compact_t(const void *in, void *out, int64_t n, int codec, Launcher &L) {
     L.begin(L.owner, CLS_SETUP, L.stream);
-    decode_copy_kernel<K><<<(unsigned)grid_for((n + 255) / 256, (int64_t)L.sms * 8), 256, 0, L.stream>>>(
-        (const K *)in, (K *)out, n, codec);
+    launch_overlapped(decode_copy_kernel<K>, (unsigned)grid_for((n + 255) / 256, (int64_t)L.sms * 8), 256, 0,
+                      L.stream, (const K *)in, (K *)out, n, codec);
     return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
 }
 
