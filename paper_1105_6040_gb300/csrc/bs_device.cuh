@@ -361,18 +361,24 @@ __device__ __forceinline__ void cand_merge_pairs(const K *sk, const uint32_t *sx
 // Sequential merge of KPT outputs from two sorted lists in padded shared
 // memory, A = S[a0, a0+m) and B = S[b0, b0+m), starting at the merge-path
 // split (i, j): each step takes the smaller head (A's on a tie) and loads
-// the next item of that list -- one shared load per output.  Reads stay in
-// [a0, b0 + m]: one past a list's end is read but not used.
+// the next item of that list -- one shared load per output.  A head past
+// its list's end reads as the largest code, so a step needs one compare:
+// while the other list has real items below the largest code they win, and
+// once its head is the largest code too every output left is that value
+// (keys only: which list supplies an equal key does not matter).  Reads stay
+// inside the two lists.
 template <class K, int KPT>
 __device__ __forceinline__ void seq_merge_keys(const K *sk, int a0, int b0, int m, int i, int j, K (&out)[KPT]) {
-    K a = sk[spad<K>(a0 + i)], b = sk[spad<K>(b0 + j)];
+    K a = i < m ? sk[spad<K>(a0 + i)] : max_code<K>();
+    K b = j < m ? sk[spad<K>(b0 + j)] : max_code<K>();
 #pragma unroll
     for (int u = 0; u < KPT; ++u) {
-        const bool tb = i >= m || (j < m && b < a);  // take B's head
+        const bool tb = b < a;  // take B's head
         out[u] = tb ? b : a;
         i += tb ? 0 : 1;
         j += tb ? 1 : 0;
-        const K nxt = sk[spad<K>(tb ? b0 + j : a0 + i)];
+        const int li = tb ? j : i;
+        const K nxt = li < m ? sk[spad<K>((tb ? b0 : a0) + li)] : max_code<K>();
         a = tb ? a : nxt;
         b = tb ? nxt : b;
     }

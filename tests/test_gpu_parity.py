@@ -122,6 +122,27 @@ def test_float_total_order_specials(sorter):
     assert np.array_equal(_bits(got), np.repeat(w, 300))
 
 
+_LARGEST = {"int32": (W.uniform_int32, np.int32, 0x7FFFFFFF),
+            "uint32": (lambda n, sd: W.uniform_int32(n, sd).view(np.uint32), np.uint32, 0xFFFFFFFF),
+            "uint64": (W.uniform_uint64, np.uint64, 0xFFFFFFFFFFFFFFFF),
+            "float32_nan": (lambda n, sd: W.uniform_int32(n, sd).view(np.uint32), np.uint32, 0x7FFFFFFF)}
+
+
+@pytest.mark.parametrize("kind", list(_LARGEST))
+@pytest.mark.parametrize("frac", [0.5, 0.97, 1.0])
+@pytest.mark.parametrize("n,p", [(T - 1, 1), (3 * T + 17, 2), (1 << 17, 8)])
+def test_largest_code_keys(sorter, kind, frac, n, p):
+    # keys whose code is the largest one -- the value padding slots and
+    # exhausted list heads read as in the tile sort and the merge passes
+    make, dt, top = _LARGEST[kind]
+    x = make(n, 23).astype(dt)
+    rng = np.random.default_rng(24)
+    x[rng.random(n) < frac] = dt(top)
+    if kind == "float32_nan":
+        x = x.view(np.float32)  # +NaN with every payload bit set is the largest float32 code
+    check_keys(sorter, x, p)
+
+
 # ------------------------------------------------------------------ stable pairs
 
 @pytest.mark.parametrize("keys", ["uniform", "zipf", "dup"])
