@@ -36,6 +36,7 @@ SIGNATURES = {
     "bs_sort_pairs": ([_P, _P, _P, _P, _P, _I64, _INT, _INT, _I64, _P], _INT),
     "bs_sort_segmented": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT, _P], _INT),
     "bs_sort_keys_host": ([_P, _P, _P, _I64, _INT, _I64], _INT),
+    "bs_sort_keys_host_async": ([_P, _P, _P, _I64, _INT, _I64, _P], _INT),
     "bs_merge_runs": ([_P, _P, _P, _P, _P, _I64, _P, _I64, _INT, _INT, _P], _INT),
     "bs_sort_segmented_gather": ([_P, _P, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT,
                                   _P], _INT),
@@ -152,6 +153,11 @@ def bs_merge_runs(h, d_kin, d_kout, d_vin, d_vout, n, h_run_offsets, runs, kt, v
 def bs_sort_keys_host(h, h_in, h_out, n, kt, p) -> None:
     _check(load().bs_sort_keys_host(h, h_in, h_out, int(n), dtype_code(kt), int(p)),
            "bs_sort_keys_host")
+
+
+def bs_sort_keys_host_async(h, h_in, h_out, n, kt, p, stream=0) -> None:
+    _check(load().bs_sort_keys_host_async(h, h_in, h_out, int(n), dtype_code(kt), int(p),
+                                          stream or None), "bs_sort_keys_host_async")
 
 
 def bs_workspace_bytes(n, S, kt, vt="none") -> int:
@@ -410,6 +416,20 @@ class Sorter:
             raise ValueError("h_in must be a contiguous CPU tensor")
         h_out = torch.empty_like(h_in) if h_out is None else h_out
         bs_sort_keys_host(self.h, h_in.data_ptr(), h_out.data_ptr(), h_in.numel(), h_in.dtype, p)
+        return h_out
+
+    def sort_keys_host_async(self, h_in, h_out, p: int = 1, stream=None):
+        """Enqueue a sort of host tensor h_in into host tensor h_out (copy in,
+        sort on `stream`, copy out) and return at once; successive calls
+        overlap their copies with each other's sorts.  The results are
+        complete after sync().  Use page-locked tensors."""
+        for t, name in ((h_in, "h_in"), (h_out, "h_out")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CPU tensor")
+        if h_out.numel() != h_in.numel() or h_out.dtype != h_in.dtype:
+            raise ValueError("h_out must match h_in in size and dtype")
+        bs_sort_keys_host_async(self.h, h_in.data_ptr(), h_out.data_ptr(), h_in.numel(), h_in.dtype, p,
+                                _stream_ptr(stream, self.device))
         return h_out
 
     def sync(self) -> None:

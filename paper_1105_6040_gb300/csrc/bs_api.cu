@@ -191,6 +191,15 @@ struct bs_handle {
     cudaStream_t own_stream = nullptr;
     void *hb = nullptr;
     size_t hb_bytes = 0;
+    // bs_sort_keys_host_async: two device buffers used in turn, a stream for
+    // the copies in and one for the copies out, and per buffer the events
+    // "copied in", "sorted", "copied out"
+    void *ab[2] = {nullptr, nullptr};
+    size_t ab_bytes[2] = {0, 0};
+    cudaStream_t cp_in = nullptr, cp_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_sorted[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
+    unsigned long long async_calls = 0;
 };
 
 namespace {
@@ -515,6 +524,14 @@ bs_status bs_destroy(bs_handle *h) {
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_counters) cudaFree(h->d_counters);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    for (int j = 0; j < 2; ++j) {
+        if (h->ab[j]) cudaFree(h->ab[j]);
+        if (h->ev_in[j]) cudaEventDestroy(h->ev_in[j]);
+        if (h->ev_sorted[j]) cudaEventDestroy(h->ev_sorted[j]);
+        if (h->ev_out[j]) cudaEventDestroy(h->ev_out[j]);
+    }
+    if (h->cp_in) cudaStreamDestroy(h->cp_in);
+    if (h->cp_out) cudaStreamDestroy(h->cp_out);
     delete h;
     return BS_OK;
 }
@@ -694,6 +711,74 @@ static void *host_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+// A device buffer of the handle, grown to `bytes` (a growing buffer waits
+// for the device first: the old one may still be in use on some stream).
+static bs_status ensure_buf(void *&buf, size_t &have, size_t bytes) {
+    if (bytes <= have) return BS_OK;
+    if (buf) {
+        cudaDeviceSynchronize();
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
+    }
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_OUT_OF_MEMORY;
+    }
+    have = bytes;
+    return BS_OK;
+}
+
+// Call k of bs_sort_keys_host_async uses device buffer j = k % 2:
+//   copy-in stream:  wait "copied out"[j] (call k-2 is done with buffer j),
+//                    copy h_in -> buffer j, record "copied in"[j];
+//   caller's stream: wait "copied in"[j] and "sorted"[1-j] (call k-1's sort:
+//                    the workspace is shared), sort in place, record "sorted"[j];
+//   copy-out stream: wait "sorted"[j], copy buffer j -> h_out, record
+//                    "copied out"[j].
+// So call k+1's copy in and call k-1's copy out run on the copy engines while
+// call k sorts.  An event not yet recorded counts as complete.
+bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
+                                  int64_t p, void *stream) {
+    if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
+    const int kw = key_width(kt);
+    if (!kw) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0) return BS_OK;
+    if (!h_in || !h_out) return BS_ERR_INVALID_ARG;
+    DevGuard dg(h->device);
+    if (!h->cp_in) {
+        if (cudaStreamCreateWithFlags(&h->cp_in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->cp_out, cudaStreamNonBlocking) != cudaSuccess)
+            return BS_ERR_CUDA;
+        for (int j = 0; j < 2; ++j)
+            if (cudaEventCreateWithFlags(&h->ev_in[j], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_sorted[j], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_out[j], cudaEventDisableTiming) != cudaSuccess)
+                return BS_ERR_CUDA;
+    }
+    const int j = (int)(h->async_calls & 1);
+    const size_t bytes = (size_t)n * kw;
+    bs_status st = ensure_buf(h->ab[j], h->ab_bytes[j], bytes);
+    if (st != BS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamWaitEvent(h->cp_in, h->ev_out[j], 0) != cudaSuccess ||
+        cudaMemcpyAsync(h->ab[j], h_in, bytes, cudaMemcpyHostToDevice, h->cp_in) != cudaSuccess ||
+        cudaEventRecord(h->ev_in[j], h->cp_in) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h->ev_in[j], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h->ev_sorted[1 - j], 0) != cudaSuccess)
+        return BS_ERR_CUDA;
+    st = bs_sort_keys(h, h->ab[j], h->ab[j], n, kt, p, (void *)s);
+    if (st != BS_OK) return st;
+    if (cudaEventRecord(h->ev_sorted[j], s) != cudaSuccess ||
+        cudaStreamWaitEvent(h->cp_out, h->ev_sorted[j], 0) != cudaSuccess ||
+        cudaMemcpyAsync(h_out, h->ab[j], bytes, cudaMemcpyDeviceToHost, h->cp_out) != cudaSuccess ||
+        cudaEventRecord(h->ev_out[j], h->cp_out) != cudaSuccess)
+        return BS_ERR_CUDA;
+    h->async_calls++;
+    h->last_stream = h->cp_out;  // bs_sync_status waits for the last copy out (and all before it)
+    return BS_OK;
+}
+
 bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
                             int64_t p) {
     if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
@@ -703,19 +788,8 @@ bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t
     if (!h_in || !h_out) return BS_ERR_INVALID_ARG;
     DevGuard dg(h->device);
     const size_t bytes = (size_t)n * kw;
-    if (bytes > h->hb_bytes) {
-        if (h->hb) {
-            cudaStreamSynchronize(h->own_stream);
-            cudaFree(h->hb);
-            h->hb = nullptr;
-            h->hb_bytes = 0;
-        }
-        if (cudaMalloc(&h->hb, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return BS_ERR_OUT_OF_MEMORY;
-        }
-        h->hb_bytes = bytes;
-    }
+    bs_status st0 = ensure_buf(h->hb, h->hb_bytes, bytes);
+    if (st0 != BS_OK) return st0;
     cudaStream_t s = h->own_stream;
     void *din = h->host_direct ? host_device_ptr(h_in) : nullptr;
     void *dout = h->host_direct ? host_device_ptr(h_out) : nullptr;

@@ -315,6 +315,37 @@ def test_host_entry_direct_and_copy(direct, case):
         s.close()
 
 
+def test_host_async_pipeline():
+    """bs_sort_keys_host_async: six calls in flight on one handle (its two
+    device buffers used in turn, copies overlapping sorts), interleaved with
+    calls on a second handle and stream; int32, float32 and uint64 keys,
+    growing sizes (a buffer regrown between calls), one call in place and
+    one from pageable memory.  Every result is the oracle's."""
+    from paper_1105_6040_gb300.abi import Sorter
+    sorters = [Sorter(0), Sorter(0)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    try:
+        xs = [W.uniform_int32((1 << 21) + 13, 111), W.normal_float32_edges(1 << 22, 112),
+              W.uniform_uint64(300007, 113), W.uniform_int32((1 << 23) + 5, 114),
+              W.dup16_int32(1 << 20, 115), W.uniform_float32_bits((1 << 22) + 99, 116),
+              W.uniform_int32(5000, 117), W.uniform_uint64((1 << 21) + 1, 118)]
+        ps = [2, 3, 1, 8, 4, 2, 1, 5]
+        ins = [torch.from_numpy(x.copy()) if k == 4 else torch.from_numpy(x.copy()).pin_memory()
+               for k, x in enumerate(xs)]
+        outs = [ins[k] if k == 3 else torch.empty_like(ins[k]).pin_memory() for k in range(len(xs))]
+        for k in range(len(xs)):
+            j = 1 if k in (2, 5) else 0  # most calls on the first handle, back to back
+            sorters[j].sort_keys_host_async(ins[k], outs[k], p=ps[k], stream=streams[j])
+        for sr in sorters:
+            sr.sync()
+        for k in range(len(xs)):
+            want = oracle.sort(xs[k], p=ps[k])[0]
+            assert np.array_equal(_bits(outs[k].numpy()), _bits(want)), k
+    finally:
+        for sr in sorters:
+            sr.close()
+
+
 def test_invalid_args(sorter):
     from paper_1105_6040_gb300 import abi
     t = torch.zeros(10, dtype=torch.int32, device="cuda")
