@@ -173,7 +173,7 @@ bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t
 /*
  * Asynchronous host-memory sort: enqueues the copy of h_in into one of the
  * handle's two device buffers (on an internal copy stream), the sort (as
- * bs_sort_keys with p blocks, on `stream`) and the copy of the result into
+ * bs_sort_keys: p blocks, Fig. 1; on `stream`) and the copy of the result into
  * h_out (may equal h_in; on a second internal copy stream), and returns.
  * Successive calls on one handle form a pipeline: call k+1's copy in and
  * call k-1's copy out run on the copy engines while call k sorts, and the
