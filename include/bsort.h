@@ -193,9 +193,10 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
 bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes);
 
 /*
- * Wait for the handle's last stream, then return the first error the GPU
- * recorded since the previous call (and clear it), else a pending CUDA error,
- * else BS_OK.
+ * Wait for the handle's last stream and for every copy out queued by
+ * bs_sort_keys_host_async, then return the first error the GPU recorded
+ * since the previous call (and clear it), else a pending CUDA error, else
+ * BS_OK.
  */
 bs_status bs_sync_status(bs_handle *h);
 

@@ -825,7 +825,10 @@ bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, siz
 bs_status bs_sync_status(bs_handle *h) {
     if (!h) return BS_ERR_INVALID_ARG;
     DevGuard dg(h->device);
-    if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) {
+    // the last stream, and the copies out of asynchronous host sorts (each
+    // waits for its sort), whichever stream the handle was used on last
+    if (cudaStreamSynchronize(h->last_stream) != cudaSuccess ||
+        (h->cp_out && cudaStreamSynchronize(h->cp_out) != cudaSuccess)) {
         cudaGetLastError();
         return BS_ERR_CUDA;
     }
