@@ -1,7 +1,9 @@
 """Autotuner for the sort's launch shapes.
 
-The tunable knobs are the sort-phase tile size T = 2^tile_log2 keys (128,
-256 or 512 threads per CTA, 16 keys per thread), the merge-pass output tile
+The tunable knobs are the sort-phase tile size T = 2^tile_log2 keys (keys
+alone: 128 or 256 threads per CTA with 32 keys each for 4096- and 8192-key
+tiles, 128 threads with 16 keys for 2048; pairs: 128, 256 or 512 threads
+with 16 pairs each), the merge-pass output tile
 (the sort tile, or 4096 keys under 8192-key sort tiles), the merge-pass
 kernel (the TMA pipeline or the plain shared-memory one) and, for the TMA
 pipeline, the keys per consumer thread (the library's choice by item size:
