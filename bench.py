@@ -328,12 +328,14 @@ def run_ours(args):
     # ---- timed region B: same steps with a CUDA event pair around every launch
     kb = min(args.steps, 20)
     abi.bs_launch_stats(sorter.h, reset=True)
+    abi.bs_set_option(sorter.h, "count_bytes", 1)
     sorter.set_timing(True)
     barrier()
     for _ in range(kb):
         step()
     barrier()
     sorter.set_timing(False)
+    abi.bs_set_option(sorter.h, "count_bytes", 0)
     kms, kn = sorter.kernel_times()
     kcounts, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
     peak, peak_src = load_peak()
@@ -488,11 +490,13 @@ def run_pairs(args):
     counts, _ = abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)
     kb = min(args.steps, 10)
     abi.bs_launch_stats(sorter.h, reset=True)
+    abi.bs_set_option(sorter.h, "count_bytes", 1)
     sorter.set_timing(True)
     for _ in range(kb):
         step()
     torch.cuda.synchronize()
     sorter.set_timing(False)
+    abi.bs_set_option(sorter.h, "count_bytes", 0)
     kms, kn = sorter.kernel_times()
     _, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
     peak, peak_src = load_peak()
@@ -602,10 +606,12 @@ def run_batched(args):
 
     # per-kernel timing of one uncaptured run
     abi.bs_launch_stats(sorter.h, reset=True)
+    abi.bs_set_option(sorter.h, "count_bytes", 1)
     sorter.set_timing(True)
     sorter.sort_segmented(d_in, d_off, kout=d_out, max_seg_len=hi)
     sorter.sync()
     sorter.set_timing(False)
+    abi.bs_set_option(sorter.h, "count_bytes", 0)
     kms, kn = sorter.kernel_times()
     kcounts, kbytes = abi.bs_launch_stats(sorter.h, reset=True)
     peak, peak_src = load_peak()

@@ -207,8 +207,9 @@ const char *bs_status_str(bs_status s);
  * Launch statistics.  counts[k] (k < BS_KERNEL_CLASSES) receives the number
  * of kernels of class k launched through this handle since creation or the
  * last reset; `bytes[k]` the algorithmic bytes those launches had to move
- * (every pass reads and writes each key and value once).  Either array may be
- * NULL.  reset != 0 zeroes the counters afterwards.
+ * (every pass reads and writes each key and value once), counted on the GPU
+ * only while BS_OPT_COUNT_BYTES is 1.  Either array may be NULL.  reset != 0
+ * zeroes the counters afterwards.
  */
 bs_status bs_launch_stats(bs_handle *h, int64_t *counts, double *bytes, int reset);
 
@@ -283,9 +284,13 @@ typedef enum {
                                 merge-path split and merges its VT outputs sequentially;
                                 1 each warp merges a slice with a bitonic merger over
                                 registers, shuffles and a shared-memory transpose */
-    BS_OPT_HOST_DIRECT = 9   /* bs_sort_keys_host: 1 (default) reads and writes page-locked
+    BS_OPT_HOST_DIRECT = 9,  /* bs_sort_keys_host: 1 (default) reads and writes page-locked
                                 host buffers directly from the kernels; 0 always copies
                                 through device memory */
+    BS_OPT_COUNT_BYTES = 10  /* 1: the kernels add every launch's algorithmic bytes to the
+                                handle's counters (one atomic per tile), which
+                                bs_launch_stats reports; 0 (default): nothing is counted
+                                and `bytes` stays at what earlier counted sorts added */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:
@@ -332,10 +337,19 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value);
  *
  * It runs on the calling thread's current CUDA device, asynchronously on
  * `stream`.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array: calls whose GPU work overlaps in
- * time (other streams or host threads on the same device) race and corrupt
- * each other's output, so serialise them.
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use the entry
+ * point across a cudaDeviceReset (the array may then live elsewhere).  All
+ * calls share the one array, which keeps the last call's contents (nothing
+ * in it needs to start at zero): calls whose GPU work overlaps in time
+ * (other streams or host threads on the same device) race and corrupt each
+ * other's output, so serialise them.
+ *
+ * Device-side errors are not reported: the call returns before its kernels
+ * run and keeps no state to query.  The only one its kernels can meet is a
+ * bounded wait running out (BS_ERR_TIMEOUT with a handle; 2 s, a GPU stalled
+ * that long), which leaves the output incomplete.  Callers that need it
+ * reported use bs_sort_keys and bs_sync_status.
  */
 #define BS_NOALLOC_MAX_KEY_BYTES (4u << 20)
 #define BS_NOALLOC_MAX_BLOCKS 1024

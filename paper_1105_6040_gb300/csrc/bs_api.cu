@@ -178,6 +178,7 @@ struct bs_handle {
     int merge_tile_log2 = 0;  // 0: the sort tile
     int merge_consumer = 0;   // 0 per-thread sequential merge, 1 warp bitonic merger
     int host_direct = 1;      // bs_sort_keys_host: address page-locked host buffers directly
+    int count_bytes = 0;      // kernels count algorithmic bytes (BS_OPT_COUNT_BYTES)
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -365,7 +366,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     g.logT = h->logT;
     g.tprefix = (const int64_t *)(ws + W.tprefix);
     g.tseg = (const int32_t *)(ws + W.tseg);
-    g.counters = h->d_counters;
+    g.counters = h->count_bytes ? h->d_counters : nullptr;
     g.err = h->d_err;
     g.wait_ns = h->wait_ns;
     g.withhold = h->withhold;
@@ -669,7 +670,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     g.logT = h->logT;
     g.R = R;
     g.ntiles_ub = 0;
-    g.counters = h->d_counters;
+    g.counters = h->count_bytes ? h->d_counters : nullptr;
     g.err = h->d_err;
     g.wait_ns = h->wait_ns;
     g.withhold = h->withhold;
@@ -949,6 +950,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value != 0 && value != 8 && value != 16 && value != 32) return BS_ERR_INVALID_ARG;
         h->merge_vt = (int)value;
         return BS_OK;
+    case BS_OPT_COUNT_BYTES:
+        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        h->count_bytes = (int)value;
+        return BS_OK;
     default:
         return BS_ERR_INVALID_ARG;
     }
@@ -995,6 +1000,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->local_sort = h->local_sort;
     g->h->merge_tile_log2 = h->merge_tile_log2;
     g->h->merge_consumer = h->merge_consumer;
+    g->h->count_bytes = h->count_bytes;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

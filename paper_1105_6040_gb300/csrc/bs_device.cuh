@@ -94,7 +94,7 @@ struct Geo {
     int64_t ntiles_ub;       // capacity of the tile arrays (bounds every tile loop)
     int logT;                // tile = 2^logT keys
     int R;                   // number of cross-block merge rounds
-    unsigned long long *counters;  // algorithmic bytes per kernel class (stats)
+    unsigned long long *counters;  // algorithmic bytes per kernel class (nullable: no counting)
     int *err;                      // device status flag (nullable): first error wins
     const int64_t *src_off;        // gathered input: segment s reads in[src_off[s] ..] (nullable)
     int64_t n_in;                  // length of the input array when src_off is set
@@ -113,6 +113,12 @@ __device__ __forceinline__ T *out_buf(bool fin, void *fin_buf, int parity, T *bu
 
 // kernel classes of the statistics counters (same order as the C ABI's)
 enum : int { CLS_TILE_SORT = 0, CLS_MERGE = 1, CLS_PARTITION = 2, CLS_SETUP = 3 };
+
+// Adds a launch's algorithmic bytes to its class counter, when counting is on
+// (g.counters set); a sort that does not count pays nothing for it.
+__device__ __forceinline__ void count_bytes(const Geo &g, int cls, unsigned long long bytes) {
+    if (g.counters) atomicAdd(g.counters + cls, bytes);
+}
 
 // Kernels launched with programmatic stream serialization may start while
 // the previous kernel on their stream finishes: they call this before
@@ -555,7 +561,7 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
                 if constexpr (HV) dst_v[base + pos] = sv[spad<V>((int)sx[spad<uint32_t>(pos)])];
             }
         }
-        if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * cnt);
+        if (tid == 0) count_bytes(g, CLS_TILE_SORT, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * cnt);
         __syncthreads();
     }
 }
@@ -621,7 +627,7 @@ tile_bubble_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int 
             const K c = sk[pos];
             dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
         }
-        if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
+        if (tid == 0) count_bytes(g, CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
         __syncthreads();
     }
 }
@@ -755,7 +761,7 @@ tile_quick_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int c
             const K c = sk[pos];
             dst[ti.base + pos] = ti.fin ? dec_code(c, codec) : c;
         }
-        if (tid == 0) atomicAdd(g.counters + CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
+        if (tid == 0) count_bytes(g, CLS_TILE_SORT, 2ull * sizeof(K) * ti.cnt);
         __syncthreads();
     }
 }
@@ -988,8 +994,7 @@ merge_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int cod
                                      out_buf<V>(p.fin, g.fin_v, p.dst, buf_v0, buf_v1), p.x0, p.fin,
                                      codec, sk, sv);
         if (threadIdx.x == 0)
-            atomicAdd(g.counters + CLS_MERGE,
-                      2ull * (sizeof(K) + (HasVal<V>::value ? sizeof(V) : 0)) * (p.x1 - p.x0));
+            count_bytes(g, CLS_MERGE, 2ull * (sizeof(K) + (HasVal<V>::value ? sizeof(V) : 0)) * (p.x1 - p.x0));
     }
 }
 
@@ -1673,8 +1678,7 @@ merge_tma_kernel(Geo g, Level L, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int
                 thread_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv,
                                             d.o_lo, fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),
                                             reinterpret_cast<uint32_t *>(ws + WS::keys));
-            if (tid == 0)
-                atomicAdd(g.counters + CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
+            if (tid == 0) count_bytes(g, CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * total_out);
         } else {
             mbar_arrive(&empty[s]);
         }

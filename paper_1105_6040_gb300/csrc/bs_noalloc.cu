@@ -20,11 +20,23 @@
 // so make the first call on a device before any stream capture.
 //
 // Sharing.  All calls in the process share the one array and it keeps the
-// contents of the previous call.  Nothing in it has to start at zero except
-// the statistics counters, which every call clears on its stream before use.
+// contents of the previous call.  Nothing in it has to start at zero: every
+// call writes each index array before reading it, and the kernels are given
+// no statistics counters (they count bytes only when handed a counter array).
 // Two calls whose GPU work overlaps in time (different streams, or different
 // host threads, on the same device) race on the array and corrupt each
 // other's results: serialise them, e.g. by issuing them on one stream.
+//
+// The cached address is only valid for the CUDA context it was looked up in:
+// after cudaDeviceReset the library's device image may load elsewhere, so do
+// not use this entry point across a cudaDeviceReset.
+//
+// Errors the GPU could find.  The merge kernels bound every wait (2 s by
+// default); a wait that runs out ends them early.  This entry point returns
+// before the GPU work runs and keeps no state a caller can query, so such a
+// timeout -- only possible on a GPU stalled for seconds -- leaves an
+// incomplete output with no error reported.  Callers that need it reported
+// use bs_sort_keys with a handle and bs_sync_status.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -40,7 +52,7 @@ __global__ void tile_map_kernel(const int64_t *tprefix, int64_t S, int32_t *tseg
 
 namespace {
 
-constexpr size_t AUX_BYTES = 64 * 1024;  // index arrays, counters
+constexpr size_t AUX_BYTES = 64 * 1024;  // index arrays (59 KiB at p = 1024, n = 2^20)
 constexpr size_t SCRATCH_BYTES = (size_t)BS_NOALLOC_MAX_KEY_BYTES + AUX_BYTES;
 constexpr int LOGT = 12;                 // tile of 4096 keys
 constexpr int SCAN_THREADS = 256;        // block size of tile_scan_block_kernel
@@ -143,19 +155,19 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
         at += up256(bytes);
         return q;
     };
-    unsigned long long *counters = (unsigned long long *)take(sizeof(unsigned long long) * 4);
     int64_t *off = (int64_t *)take(sizeof(int64_t) * (p + 1));
     int64_t *tprefix = (int64_t *)take(sizeof(int64_t) * (p + 1));
     int64_t *bsum = (int64_t *)take(sizeof(int64_t) * 2);
     int32_t *tseg = (int32_t *)take(sizeof(int32_t) * ub);
-    const int64_t xt = bs::xblock_tiles_max(n, p, LOGT);
+    // one merge-path split per merge tile (+1): merge tiles may be as small as
+    // 2^11 keys (the pass planner shrinks them when a shape's stages do not fit),
+    // so size for that -- the cross-block rounds' tiles, and the in-block levels'
+    // (n / 2^11 + 4 (p + 1)) -- as the handle's workspace does
+    int64_t xt = bs::xblock_tiles_max(n, p, 11);
+    const int64_t seg_merge_tiles = (n + 2047) / 2048 + 4 * (p + 1);
+    if (seg_merge_tiles > xt) xt = seg_merge_tiles;
     int64_t *split = (int64_t *)take(sizeof(int64_t) * ((ub > xt ? ub : xt) + 1));
     if (at > SCRATCH_BYTES) return BS_ERR_TOO_LARGE;  // cannot happen within the limits above
-
-    if (cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 4, s) != cudaSuccess) {
-        cudaGetLastError();
-        return BS_ERR_CUDA;
-    }
 
     bs::Geo g{};
     g.off = off;
@@ -166,7 +178,8 @@ extern "C" bs_status bs_sort_keys_noalloc(const void *d_in, void *d_out, int64_t
     g.ntiles_ub = ub;
     g.logT = LOGT;
     g.R = ceil_log2(p);
-    g.counters = counters;
+    g.counters = nullptr;  // no byte counting
+    g.err = nullptr;       // no status word: see "Errors the GPU could find" above
 
     // scatter bounds, tiles per block (p <= 1024 fits one scan block), tile map
     const unsigned pb = (unsigned)((p + 1 + 255) / 256);

@@ -364,11 +364,19 @@ def test_invalid_args(sorter):
 def test_launch_stats_count_passes(sorter):
     sorter.stats(reset=True)
     n = 1 << 20
-    sorter.sort_keys(_to_dev(W.uniform_int32(n, 91)), p=2)
-    counts, byts = sorter.stats(reset=True)
+    abi.bs_set_option(sorter.h, "count_bytes", 1)
+    try:
+        sorter.sort_keys(_to_dev(W.uniform_int32(n, 91)), p=2)
+        counts, byts = sorter.stats(reset=True)
+    finally:
+        abi.bs_set_option(sorter.h, "count_bytes", 0)
     # 1 tile-sort pass + 7 in-block levels (2^19 / 4096 = 2^7 tiles) + 1 cross round
     assert counts["tile_sort"] == 1 and counts["merge"] == 8
     assert byts["tile_sort"] == 2 * 4 * n and byts["merge"] == 8 * 2 * 4 * n
+    # counting off (the default): the same sort adds no bytes
+    sorter.sort_keys(_to_dev(W.uniform_int32(n, 92)), p=2)
+    counts, byts = sorter.stats(reset=True)
+    assert counts["merge"] == 8 and byts["tile_sort"] == 0 and byts["merge"] == 0
 
 
 # ------------------------------------------------------------------ full sizes
