@@ -287,10 +287,17 @@ typedef enum {
     BS_OPT_HOST_DIRECT = 9,  /* bs_sort_keys_host: 1 (default) reads and writes page-locked
                                 host buffers directly from the kernels; 0 always copies
                                 through device memory */
-    BS_OPT_COUNT_BYTES = 10  /* 1: the kernels add every launch's algorithmic bytes to the
+    BS_OPT_COUNT_BYTES = 10, /* 1: the kernels add every launch's algorithmic bytes to the
                                 handle's counters (one atomic per tile), which
                                 bs_launch_stats reports; 0 (default): nothing is counted
                                 and `bytes` stays at what earlier counted sorts added */
+    BS_OPT_MERGE_PERSISTENT = 11 /* 1 (default): every merge pass of a sort (the in-block
+                                levels and the merge phase's rounds) runs in ONE persistent
+                                launch whose CTAs take merge tiles from a work queue in
+                                device memory, each tile starting once the runs it reads
+                                are complete; it applies with the default merge consumer
+                                and keys per thread, the tree schedule and 16-byte aligned
+                                buffers.  0: one partition and one merge launch per pass */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

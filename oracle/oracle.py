@@ -24,7 +24,7 @@ from . import build as _build
 __all__ = [
     "OracleLib", "load", "encode", "decode", "sort", "sort_segmented",
     "is_nondecreasing", "multiset_hash", "rank_bounds", "block_bounds",
-    "DTYPES", "LOCAL", "FORMS",
+    "DTYPES", "LOCAL", "FORMS", "default_threads",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "float32": 2, "int64": 3, "uint64": 4, "float64": 5}

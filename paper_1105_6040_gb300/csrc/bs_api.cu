@@ -179,6 +179,7 @@ struct bs_handle {
     int merge_consumer = 0;   // 0 per-thread sequential merge, 1 warp bitonic merger
     int host_direct = 1;      // bs_sort_keys_host: address page-locked host buffers directly
     int count_bytes = 0;      // kernels count algorithmic bytes (BS_OPT_COUNT_BYTES)
+    int persistent = 1;       // every merge level in one persistent launch (BS_OPT_MERGE_PERSISTENT)
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -246,7 +247,8 @@ bool launch_end(void *owner, int cls, cudaStream_t s) {
 }
 
 struct WsLayout {
-    size_t tmp_k, tmp_v, off, tprefix, bsum, tseg, split, total;
+    size_t tmp_k, tmp_v, off, tprefix, bsum, tseg, split, pcnt, total;
+    int64_t pcnt_words;
 };
 
 constexpr int64_t MIN_TILE = 2048;
@@ -274,6 +276,13 @@ WsLayout ws_layout(int64_t n, int64_t S, size_t ks, size_t vs, int64_t extra_til
     if (seg_merge_tiles > xt) xt = seg_merge_tiles;
     L.tseg = take((size_t)ub * 4);
     L.split = take((size_t)((ub > xt ? ub : xt) + 1) * 8);
+    // persistent merge: work queue + pair counters, for the largest in-block
+    // level count any tile size gives (levels of 2^11-key tiles)
+    int lv = 0, R = 0;
+    while ((int64_t(MIN_TILE) << lv) < n) ++lv;
+    while ((int64_t(1) << R) < S) ++R;
+    L.pcnt_words = persist_words(lv, ub, R, S);
+    L.pcnt = take((size_t)L.pcnt_words * 4);
     L.total = o;
     return L;
 }
@@ -375,6 +384,21 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
 
     Launcher L{stream, h, h->sms, launch_begin, launch_end};
     int codec = key_codec(kt);
+    // the persistent merge's queue head and pair counters start at zero
+    const int64_t T0 = int64_t(1) << g.logT;
+    const int64_t ub0 = (n + T0 - 1) / T0 + blocks;
+    int64_t Lmax0 = 0;
+    if (balanced) {
+        Lmax0 = levels_for((n + p - 1) / p, g.logT);
+    } else {
+        const int64_t lim = (max_len > 0 && max_len < n) ? max_len : n;
+        Lmax0 = levels_for(lim, g.logT);
+    }
+    const bool persist = h->persistent && !oddeven;
+    const int64_t pwords = persist_words((int)Lmax0, ub0, g.R, blocks);
+    if (persist && pwords <= W.pcnt_words &&
+        cudaMemsetAsync(ws + W.pcnt, 0, (size_t)pwords * 4, stream) != cudaSuccess)
+        return BS_ERR_CUDA;
     if (oddeven) {
         // scatter + encode into the padded buffer A; then sort A in place
         void *A = ws + W.total;
@@ -461,6 +485,9 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.local_sort = h->local_sort;
     a.merge_tile_log2 = h->merge_tile_log2;
     a.merge_consumer = h->merge_consumer;
+    a.persistent = persist && pwords <= W.pcnt_words;
+    a.pcnt = (unsigned *)(ws + W.pcnt);
+    a.pcnt_words = pwords;
     st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
     if (st != BS_OK || !oddeven) return st;
     // after p rounds the keys are in buffer (p & 1): decode the first n
@@ -663,6 +690,9 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     if (cudaMemcpyAsync(off, h_run_offsets, sizeof(int64_t) * (runs + 1), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return BS_ERR_CUDA;
+    const int64_t pwords = persist_words(0, 0, R, runs);
+    const bool persist = h->persistent && pwords <= W.pcnt_words;
+    if (persist && cudaMemsetAsync(ws + W.pcnt, 0, (size_t)pwords * 4, s) != cudaSuccess) return BS_ERR_CUDA;
     Geo g{};
     g.off = off;
     g.S = runs;
@@ -698,6 +728,9 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.local_sort = 0;
     a.merge_tile_log2 = h->merge_tile_log2;
     a.merge_consumer = h->merge_consumer;
+    a.persistent = persist;
+    a.pcnt = (unsigned *)(ws + W.pcnt);
+    a.pcnt_words = pwords;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
 }
 
@@ -954,6 +987,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
         h->count_bytes = (int)value;
         return BS_OK;
+    case BS_OPT_MERGE_PERSISTENT:
+        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        h->persistent = (int)value;
+        return BS_OK;
     default:
         return BS_ERR_INVALID_ARG;
     }
@@ -1001,6 +1038,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->merge_tile_log2 = h->merge_tile_log2;
     g->h->merge_consumer = h->merge_consumer;
     g->h->count_bytes = h->count_bytes;
+    g->h->persistent = h->persistent;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -1136,8 +1136,9 @@ struct StageDesc {
     int64_t o_lo;
     int a_off, na, b_off, nb;  // key windows
     int av_off, bv_off;        // value windows
-    int flags;                 // bit0 active, bit1 dst parity, bit2 final pass
+    int flags;                 // bit0 active, bit1 dst parity, bit2 final pass (bit3: no more tiles)
     int pad;
+    unsigned *ctr;             // persistent merge: the pair counter that counts this tile done
 };
 
 // One stage holds the tile's A and B windows back to back (B's starts at the

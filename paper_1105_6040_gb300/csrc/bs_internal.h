@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "bs_device.cuh"
+#include "bs_persist.cuh"
 #include "bsort.h"
 
 namespace bs {
@@ -58,7 +59,23 @@ struct PassArgs {
     int local_sort;           // tile sort: 0 network + merges, 1 bubble (Fig. 2), 2 quick (Fig. 4)
     int merge_tile_log2;      // merge-pass tile (0: the sort tile; else 11 .. logT)
     int merge_consumer;       // TMA merge consumers: 0 per-thread sequential merge, 1 warp bitonic
+    int persistent;           // 1: every merge level in one persistent launch where it can run
+    unsigned *pcnt;           // its pair counters and work queue (zeroed before the sort phase)
+    int64_t pcnt_words;       // capacity of pcnt in 32-bit words
 };
+
+// Words of the persistent merge's counter region for a sort whose in-block
+// levels number `nseg` over `ntiles_ub` sort tiles in S blocks and whose
+// merge phase has R rounds: the work-queue head (2 words), a row per
+// in-block level lv of ntiles_ub / 2^(lv+1) + S + 2 pair counters, then one
+// counter per pair of every cross-block round.
+inline int64_t persist_seg_row(int64_t ntiles_ub, int64_t S, int lv) { return (ntiles_ub >> (lv + 1)) + S + 2; }
+inline int64_t persist_words(int nseg, int64_t ntiles_ub, int R, int64_t S) {
+    int64_t w = 2;
+    for (int lv = 0; lv < nseg; ++lv) w += persist_seg_row(ntiles_ub, S, lv);
+    for (int r = 0; r < R; ++r) w += (S + (int64_t(2) << r) - 1) >> (r + 1);
+    return w;
+}
 
 enum : int { MERGE_AUTO = 0, MERGE_SIMPLE = 1, MERGE_TMA = 2 };
 

@@ -156,6 +156,92 @@ bool merge_pass_any(const PassArgs &a, Launcher &L, const Level &lvl, int64_t ti
     return L.end(L.owner, CLS_MERGE, L.stream);
 }
 
+// The persistent merge (every level in one launch) at shape (MT consumer
+// threads, MVT keys each): launches it and returns 1, returns 0 when it cannot
+// run here (shared memory, or above the automatic limit), -1 when the launch
+// failed.
+template <class K, class V, int MT, int MVT>
+int launch_merge_persist_at(const PassArgs &a, Launcher &L, const PersistPlan &P, int64_t batches) {
+    auto kern = merge_persist_kernel<K, V, MT, MVT, MERGE_STAGES>;
+    constexpr size_t smem = persist_smem_bytes<K, V, MT, MVT, MERGE_STAGES>();
+    static std::atomic<int> occ{0};
+    if (!occ.load()) {
+        if (smem <= SMEM_OPT_IN_LIMIT && allow_smem(kern, smem))
+            occ.store(resident_ctas(kern, MT + 64, smem));
+        else
+            occ.store(-1);
+    }
+    if (occ.load() <= 0) return 0;
+    if (a.merge_impl == MERGE_AUTO && smem > TMA_SMEM_AUTO_LIMIT) return 0;
+    // every resident CTA (the queue balances the work), no more than there are batches
+    const int64_t grid = grid_for(batches, (int64_t)L.sms * occ.load());
+    PersistPlan Pm = P;
+    Pm.ncw = MT / 32;
+    L.begin(L.owner, CLS_MERGE, L.stream);
+    launch_overlapped(kern, (unsigned)grid, MT + 64, smem, L.stream, a.g, Pm, (K *)a.k0, (K *)a.k1, (V *)a.v0,
+                      (V *)a.v1, a.codec, a.ntiles_total);
+    return L.end(L.owner, CLS_MERGE, L.stream) ? 1 : -1;
+}
+
+// Every merge level of the sort (nseg in-block levels, then the g.R
+// cross-block rounds) in one persistent launch; the same return values.
+// Runs only the default consumer (sequential merge) at the default keys per
+// thread; other shapes take the per-pass path.
+template <class K, class V>
+int launch_merge_persist(const PassArgs &a, Launcher &L, int nseg, int mlogT) {
+    const Geo &g = a.g;
+    if (a.merge_consumer != 0 || (a.merge_vt && a.merge_vt != merge_vt_of<K, V>(PassArgs{})) || !a.pcnt)
+        return 0;
+    PersistPlan P{};
+    P.nseg = nseg;
+    P.nl = nseg + g.R;
+    P.mlogT = mlogT;
+    if (P.nl > PERSIST_MAX_LEVELS) return 0;
+    if (P.nl == 0) return 1;  // nothing to merge
+    if (persist_words(nseg, g.ntiles_ub, g.R, g.S) > a.pcnt_words) return 0;
+    P.work = reinterpret_cast<unsigned long long *>(a.pcnt);
+    P.cnt_seg = a.pcnt + 2;
+    int64_t rows = 0;
+    for (int lv = 0; lv < nseg; ++lv) {
+        P.segrow[lv] = rows;
+        rows += persist_seg_row(g.ntiles_ub, g.S, lv);
+    }
+    P.cnt_x = P.cnt_seg + rows;
+    int64_t batches = 0, xoff = 0;
+    const int64_t seg_tiles = a.ntiles_ub << (g.logT - mlogT);  // an upper bound (grid sizing only)
+    batches += (int64_t)nseg * ((seg_tiles + PERSIST_BATCH - 1) / PERSIST_BATCH);
+    for (int r = 0; r < g.R; ++r) {
+        int64_t tpp = 0, nt = 0;
+        const int64_t npairs = (g.S + (int64_t(2) << r) - 1) >> (r + 1);
+        if (a.tpp_host) {
+            tpp = a.tpp_host[r] << (g.logT - mlogT);
+            nt = npairs * tpp;
+        } else {
+            nt = xblock_tiles(g.n, g.S, r, mlogT, &tpp);
+        }
+        P.xtiles[r] = nt;
+        P.xtpp[r] = tpp;
+        P.xcnt[r] = xoff;
+        xoff += npairs;
+        batches += (nt + PERSIST_BATCH - 1) / PERSIST_BATCH;
+    }
+    if constexpr (sizeof(K) == 4 && !HasVal<V>::value) {  // 32 keys per consumer thread
+        switch (mlogT) {
+        case 11: return launch_merge_persist_at<K, V, 64, 32>(a, L, P, batches);
+        case 12: return launch_merge_persist_at<K, V, 128, 32>(a, L, P, batches);
+        case 13: return launch_merge_persist_at<K, V, 256, 32>(a, L, P, batches);
+        default: return 0;
+        }
+    } else {  // 16
+        switch (mlogT) {
+        case 11: return launch_merge_persist_at<K, V, 128, 16>(a, L, P, batches);
+        case 12: return launch_merge_persist_at<K, V, 256, 16>(a, L, P, batches);
+        case 13: return launch_merge_persist_at<K, V, 512, 16>(a, L, P, batches);
+        default: return 0;
+        }
+    }
+}
+
 template <class K, class V, int THREADS, int KPT>
 bs_status run_passes_t(const PassArgs &a, Launcher &L) {
     constexpr int T = THREADS * KPT;
@@ -215,6 +301,13 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
                           L.stream, g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec,
                           a.ntiles_total);
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+    }
+
+    // every merge level in one persistent launch, where it can run
+    if (a.persistent && a.merge_impl != MERGE_SIMPLE && a.oddeven_rounds == 0) {
+        const int pr = launch_merge_persist<K, V>(a, L, a.Lmax, mlogT);
+        if (pr < 0) return BS_ERR_CUDA;
+        if (pr > 0) return BS_OK;
     }
 
     // sort phase, continued: in-block merge levels

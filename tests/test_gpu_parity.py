@@ -362,21 +362,82 @@ def test_invalid_args(sorter):
 
 
 def test_launch_stats_count_passes(sorter):
-    sorter.stats(reset=True)
+    """1 tile-sort pass + 7 in-block levels (2^19 / 4096 = 2^7 tiles) + 1 cross
+    round: one persistent merge launch by default, 8 partition + 8 merge
+    launches per pass otherwise; the algorithmic bytes are the same."""
+    from paper_1105_6040_gb300 import abi
     n = 1 << 20
-    abi.bs_set_option(sorter.h, "count_bytes", 1)
-    try:
-        sorter.sort_keys(_to_dev(W.uniform_int32(n, 91)), p=2)
-        counts, byts = sorter.stats(reset=True)
-    finally:
-        abi.bs_set_option(sorter.h, "count_bytes", 0)
-    # 1 tile-sort pass + 7 in-block levels (2^19 / 4096 = 2^7 tiles) + 1 cross round
-    assert counts["tile_sort"] == 1 and counts["merge"] == 8
-    assert byts["tile_sort"] == 2 * 4 * n and byts["merge"] == 8 * 2 * 4 * n
+    for persistent, merges, parts in ((1, 1, 0), (0, 8, 8)):
+        abi.bs_set_option(sorter.h, "merge_persistent", persistent)
+        sorter.stats(reset=True)
+        abi.bs_set_option(sorter.h, "count_bytes", 1)
+        try:
+            sorter.sort_keys(_to_dev(W.uniform_int32(n, 91)), p=2)
+            counts, byts = sorter.stats(reset=True)
+        finally:
+            abi.bs_set_option(sorter.h, "count_bytes", 0)
+            abi.bs_set_option(sorter.h, "merge_persistent", 1)
+        assert counts["tile_sort"] == 1 and counts["merge"] == merges and counts["partition"] == parts
+        assert byts["tile_sort"] == 2 * 4 * n and byts["merge"] == 8 * 2 * 4 * n
     # counting off (the default): the same sort adds no bytes
     sorter.sort_keys(_to_dev(W.uniform_int32(n, 92)), p=2)
     counts, byts = sorter.stats(reset=True)
-    assert counts["merge"] == 8 and byts["tile_sort"] == 0 and byts["merge"] == 0
+    assert counts["merge"] == 1 and byts["tile_sort"] == 0 and byts["merge"] == 0
+
+
+@pytest.mark.parametrize("tile_log2,merge_tile_log2", [(12, 0), (13, 11), (11, 11), (13, 13)])
+def test_persistent_merge_matches_per_pass_and_oracle(tile_log2, merge_tile_log2):
+    """The persistent merge (every level in one launch, tiles waiting on the
+    pairs they read) against the per-pass kernels and the oracle: balanced
+    blocks at p up to 4096 and not powers of two, keys of every width, stable
+    pairs, segmented batches whose short segments leave most upper-level tiles
+    inactive, merge-only runs; each case run three times on one handle."""
+    from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300.abi import Sorter
+    per = Sorter(0, tile_log2=tile_log2, merge_tile_log2=merge_tile_log2)
+    abi.bs_set_option(per.h, "merge_persistent", 0)
+    pst = Sorter(0, tile_log2=tile_log2, merge_tile_log2=merge_tile_log2)
+    try:
+        for n, p in ((1, 1), (T - 1, 1), (3 * T + 7, 2), (100003, 3), (1 << 18, 6), (262139, 4096),
+                     ((1 << 20) + 5, 7), (1 << 21, 1)):
+            for x in (W.uniform_int32(n, n + p), W.uniform_uint64(n, n + p + 1)):
+                want, _ = oracle.sort(x, p=min(p, n), threads=8)
+                a = gpu_keys(per, x, p)
+                assert np.array_equal(_bits(a), _bits(want)), (n, p, "per-pass")
+                for _ in range(3):
+                    b = gpu_keys(pst, x, p)
+                    assert np.array_equal(_bits(b), _bits(want)), (n, p, "persistent")
+        for kmaker, vmaker in ((lambda n: W.uniform_int32(n, 8) % 300, W.index_payload),
+                               (lambda n: W.zipf_uint64(n, 7), lambda n: W.uniform_uint64(n, 9))):
+            n, p = 300007, 5
+            k, v = kmaker(n), vmaker(n)
+            wk, wv = oracle.sort(k, v, p=p)
+            for _ in range(3):
+                ko, vo = pst.sort_pairs(_to_dev(k), _to_dev(v), p=p)
+                pst.sync()
+                assert np.array_equal(_bits(_to_host(ko)), _bits(wk))
+                assert np.array_equal(_bits(_to_host(vo)), _bits(wv))
+        lens = W.loguniform_lengths(3000, 1, 1 << 17, seed=79)
+        off = W.offsets_from_lengths(lens)
+        k = W.uniform_int32(int(off[-1]), seed=80)
+        want = oracle.sort_segmented(k, off)[0]
+        for _ in range(3):
+            res = pst.sort_segmented(_to_dev(k), torch.from_numpy(off).cuda())
+            pst.sync()
+            assert np.array_equal(_to_host(res), want)
+        # merge phase only: 37 caller-sorted runs of uneven length, some empty
+        rl = W.loguniform_lengths(37, 1, 1 << 15, seed=81)
+        rl[[3, 17]] = 0
+        roff = W.offsets_from_lengths(rl)
+        x = W.uniform_int32(int(roff[-1]), seed=82)
+        runs = np.concatenate([np.sort(x[roff[i]:roff[i + 1]]) for i in range(len(rl))])
+        for _ in range(3):
+            out = pst.merge_runs(_to_dev(runs), [int(v) for v in roff])
+            pst.sync()
+            assert np.array_equal(_to_host(out), np.sort(x))
+    finally:
+        per.close()
+        pst.close()
 
 
 # ------------------------------------------------------------------ full sizes
@@ -513,13 +574,17 @@ def test_unaligned_buffers_fall_back(sorter):
 
 # ------------------------------------------------------------------ failure detection
 
-def test_bounded_wait_runs_out_and_reports_timeout():
-    """A stage that nothing fills: the merge pass's bounded waits run out, the
-    call reports BS_ERR_TIMEOUT, and the same handle sorts correctly after."""
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_bounded_wait_runs_out_and_reports_timeout(persistent):
+    """A stage that nothing fills: the merge's bounded waits run out (in the
+    persistent merge, the other CTAs' waits on the pairs that CTA never
+    finishes too), the call reports BS_ERR_TIMEOUT, and the same handle sorts
+    correctly after."""
     from paper_1105_6040_gb300 import abi
     from paper_1105_6040_gb300.abi import Sorter
     s = Sorter(0, merge_kernel="tma")
     try:
+        abi.bs_set_option(s.h, "merge_persistent", persistent)
         x = W.uniform_int32(1 << 16, seed=123)
         d = _to_dev(x)
         abi.bs_set_option(s.h, "wait_limit_ms", 100)
