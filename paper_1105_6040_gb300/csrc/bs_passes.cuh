@@ -167,7 +167,7 @@ int launch_merge_persist_at(const PassArgs &a, Launcher &L, const PersistPlan &P
     static std::atomic<int> occ{0};
     if (!occ.load()) {
         if (smem <= SMEM_OPT_IN_LIMIT && allow_smem(kern, smem))
-            occ.store(resident_ctas(kern, MT + 64, smem));
+            occ.store(resident_ctas(kern, persist_block<MT>(), smem));
         else
             occ.store(-1);
     }
@@ -176,9 +176,9 @@ int launch_merge_persist_at(const PassArgs &a, Launcher &L, const PersistPlan &P
     // every resident CTA (the queue balances the work), no more than there are batches
     const int64_t grid = grid_for(batches, (int64_t)L.sms * occ.load());
     PersistPlan Pm = P;
-    Pm.ncw = MT / 32;
+    Pm.ncw = 1;  // the producer counts each tile once
     L.begin(L.owner, CLS_MERGE, L.stream);
-    launch_overlapped(kern, (unsigned)grid, MT + 64, smem, L.stream, a.g, Pm, (K *)a.k0, (K *)a.k1, (V *)a.v0,
+    launch_overlapped(kern, (unsigned)grid, persist_block<MT>(), smem, L.stream, a.g, Pm, (K *)a.k0, (K *)a.k1, (V *)a.v0,
                       (V *)a.v1, a.codec, a.ntiles_total);
     return L.end(L.owner, CLS_MERGE, L.stream) ? 1 : -1;
 }

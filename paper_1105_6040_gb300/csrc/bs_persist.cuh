@@ -24,9 +24,12 @@
 //   producer warp  stages each tile's A and B slices into the stage ring by
 //                  1-D bulk copies (TMA), as the per-pass TMA merge does;
 //   consumers      merge the staged tile (the same consumer code as the
-//                  per-pass kernel), store it, and count it done on its
-//                  pair's counter (release); the search warp reads counters
-//                  with acquire loads.
+//                  per-pass kernel), store it and count their part stored in
+//                  shared memory; whenever the search warp would wait, it
+//                  releases the stored tiles at GPU scope and counts them done
+//                  on their pairs' counters, which search warps read with
+//                  acquire loads (a release waits for the stores to land, ~2 us,
+//                  so it is kept off the warps that move data).
 // Data written by one CTA's stores is read by another CTA's bulk copies and
 // search loads: the writer releases after its stores, the reader acquires
 // before its loads, search and tail loads bypass L1 (ld.global.cg), and the
@@ -41,7 +44,7 @@
 namespace bs {
 
 constexpr int PERSIST_MAX_LEVELS = 48;
-constexpr int PERSIST_BATCH = 7;  // merge tiles per work item: 8 boundaries x 4 search lanes
+constexpr int PERSIST_BATCH = 15;  // merge tiles per work item: 16 boundaries x 2 search lanes
 constexpr int PERSIST_SLOTS = 2;  // batch slots between the search warp and the producer
 
 // Everything the persistent merge needs besides Geo and the buffers.
@@ -50,8 +53,7 @@ struct PersistPlan {
     int nseg;    // levels 0 .. nseg-1 are in-block levels (LEVEL_SEG lv = l), the rest
                  // cross-block rounds (LEVEL_XBLOCK r = l - nseg)
     int mlogT;   // merge tile = 2^mlogT keys
-    int ncw;     // increments a completed merge tile adds to its pair counter (one per
-                 // consumer warp)
+    int ncw;     // increments a completed merge tile adds to its pair counter (1)
     int64_t xtiles[PERSIST_MAX_LEVELS];  // cross-block round r: its merge tiles
     int64_t xtpp[PERSIST_MAX_LEVELS];    // cross-block round r: merge tiles per pair
     int64_t xcnt[PERSIST_MAX_LEVELS];    // cross-block round r: first of its counters in cnt_x
@@ -212,16 +214,43 @@ struct BatchSlot {
 
 constexpr int STAGE_STOP = 8;  // StageDesc flag: no more tiles
 
+constexpr int PERSIST_PEND = 32;  // tiles staged but not yet counted done, at most
+
+// Shared state between the consumers, the producer and the signal thread.
+struct SignalRing {
+    unsigned *ctr[PERSIST_PEND];  // pair counter of staged tile j, at j % PERSIST_PEND
+    unsigned done[32];            // tiles consumer warp w has stored (monotone)
+    unsigned retired;             // tiles counted done
+    unsigned final_tiles;         // tiles staged in all, once the producer stops (~0u before)
+};
+
 template <class K, class V, int THREADS, int VT, int STAGES>
 __host__ __device__ constexpr size_t persist_smem_bytes() {
     return STAGES * TmaLayout<K, V, THREADS * VT>::stage + (THREADS / 32) * WarpScratch<K, V, VT>::bytes +
-           PERSIST_SLOTS * sizeof(BatchSlot) + 2 * (STAGES + PERSIST_SLOTS) * sizeof(uint64_t) + 128;
+           PERSIST_SLOTS * sizeof(BatchSlot) + (2 * STAGES + 2 * PERSIST_SLOTS) * sizeof(uint64_t) +
+           sizeof(SignalRing) + 128;
 }
+
+__device__ __forceinline__ void red_release_cta_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cta(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(unsigned *p, unsigned v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+// Threads of a persistent-merge CTA: consumers, then the producer and search
+// warps.
+template <int THREADS> constexpr int persist_block() { return THREADS + 64; }
 
 template <class K, class V, int THREADS, int VT, int STAGES> constexpr int persist_min_ctas() {
     const int by_smem = (int)((228 * 1024) / (persist_smem_bytes<K, V, THREADS, VT, STAGES>() + 1024));
     const int regs = 64;
-    const int by_regs = 65536 / ((THREADS + 64) * regs);
+    const int by_regs = 65536 / (persist_block<THREADS>() * regs);
     const int m = by_smem < by_regs ? by_smem : by_regs;
     return m < 1 ? 1 : m;
 }
@@ -229,7 +258,7 @@ template <class K, class V, int THREADS, int VT, int STAGES> constexpr int persi
 // ---------------------------------------------------------------- the kernel
 
 template <class K, class V, int THREADS, int VT, int STAGES>
-__global__ void __launch_bounds__(THREADS + 64, (persist_min_ctas<K, V, THREADS, VT, STAGES>()))
+__global__ void __launch_bounds__(persist_block<THREADS>(), (persist_min_ctas<K, V, THREADS, VT, STAGES>()))
 merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
                      const int64_t *__restrict__ ntiles_total) {
     constexpr int TT = THREADS * VT;
@@ -242,10 +271,13 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
     constexpr size_t SCRATCH = (THREADS / 32) * WS::bytes;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BatchSlot *slots = reinterpret_cast<BatchSlot *>(smem_raw + STAGES * LY::stage + SCRATCH);
+    constexpr int NCW = THREADS / 32;
+    static_assert(NCW <= 32, "consumer warps fit the signal ring");
     uint64_t *full = reinterpret_cast<uint64_t *>(slots + PERSIST_SLOTS);
     uint64_t *empty = full + STAGES;
     uint64_t *sfull = empty + STAGES;
     uint64_t *sempty = sfull + PERSIST_SLOTS;
+    SignalRing *ring = reinterpret_cast<SignalRing *>(sempty + PERSIST_SLOTS);
     auto stage_k = [&](int s) { return reinterpret_cast<K *>(smem_raw + s * LY::stage); };
     auto stage_v = [&](int s) { return reinterpret_cast<V *>(smem_raw + s * LY::stage + LY::keys); };
     auto stage_desc = [&](int s) {
@@ -257,6 +289,9 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], THREADS);
         }
+        for (int w = 0; w < 32; ++w) ring->done[w] = 0;
+        ring->retired = 0;
+        ring->final_tiles = ~0u;
         for (int s = 0; s < PERSIST_SLOTS; ++s) {
             mbar_init(&sfull[s], 1);
             mbar_init(&sempty[s], 1);
@@ -280,6 +315,46 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
         int slot = 0;
         uint32_t sph = 0;  // phase of the slot's "empty" barrier we wait for
         uint64_t nbatch = 0;
+        // Counting the CTA's stored tiles done (lane 0), whenever the warp would
+        // otherwise wait: a GPU-scope fence (the consumers' stores, acquired
+        // through their counts, before anything after it) and the pair
+        // counters' increments.  The fence waits for the stores to land (~2 us),
+        // so it is kept off the warps that move data.  Returns true if any tile
+        // was counted.
+        unsigned retired = 0;
+        auto signal = [&]() -> bool {
+            bool any = false;
+            if (lane == 0) {
+                unsigned m = ~0u;
+                for (int w = 0; w < NCW; ++w) {
+                    const unsigned d = ld_acquire_cta(&ring->done[w]);
+                    m = d < m ? d : m;
+                }
+                if (m != retired) {
+                    __threadfence();
+                    fence_proxy_async_global();
+                    for (; retired != m; ++retired) atomicAdd(ring->ctr[retired % PERSIST_PEND], 1u);
+                    st_release_cta(&ring->retired, retired);
+                    any = true;
+                }
+            }
+            return __shfl_sync(FULL, (int)any, 0) != 0;
+        };
+        // after the last batch: count every tile the producer staged, then leave
+        auto finish = [&]() {
+            uint64_t t0 = global_ns();
+            for (uint32_t i = 1;; ++i) {
+                if (signal()) t0 = global_ns();
+                const bool all = __shfl_sync(FULL, (int)(ld_acquire_cta(&ring->final_tiles) == retired), 0) != 0;
+                if (all) return;
+                if ((i & 15) == 0 &&
+                    __shfl_sync(FULL, (int)(global_ns() - t0 > WAIT_LIMIT), 0) != 0) {
+                    if (lane == 0 && g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
+                    return;
+                }
+                __nanosleep(200);
+            }
+        };
         for (;;) {
             // ---- pop a batch and find its level
             unsigned long long b = 0;
@@ -314,6 +389,7 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                     const uint64_t t0 = global_ns();
                     bool timed_out = false;
                     for (uint32_t it = 1; !__all_sync(FULL, ok); ++it) {
+                        signal();  // this CTA's own tiles may be among those awaited
                         if (!ok) ok = deps_done(dp);
                         if ((it & 15) == 0) {
                             timed_out = __shfl_sync(FULL, (int)(global_ns() - t0 > WAIT_LIMIT), 0) != 0;
@@ -363,9 +439,22 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                 split = ps + lo;
             }
             // ---- hand the batch to the producer
-            if (nbatch >= PERSIST_SLOTS && !mbar_wait(&sempty[slot], sph ^ 1u, WAIT_LIMIT)) {
-                if (lane == 0 && g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
-                return;  // the producer is gone or stuck: it times out on its own
+            if (nbatch >= PERSIST_SLOTS && !mbar_try_wait(&sempty[slot], sph ^ 1u)) {
+                const uint64_t t0 = global_ns();
+                bool timed_out = false;
+                for (uint32_t i = 1; !mbar_try_wait(&sempty[slot], sph ^ 1u); ++i) {
+                    signal();
+                    if ((i & 15) == 0 &&
+                        __shfl_sync(FULL, (int)(global_ns() - t0 > WAIT_LIMIT), 0) != 0) {
+                        timed_out = true;
+                        break;
+                    }
+                }
+                if (timed_out) {
+                    if (lane == 0 && g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
+                    finish();
+                    return;  // the producer is gone or stuck: it times out on its own
+                }
             }
             const int64_t s_lo = __shfl_sync(FULL, split, (lane < PERSIST_BATCH ? lane : 0) * GS);
             const int64_t s_hi = __shfl_sync(FULL, split, (lane < PERSIST_BATCH ? lane + 1 : 0) * GS);
@@ -392,28 +481,49 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
             ++nbatch;
             sph ^= (slot == PERSIST_SLOTS - 1);
             slot = (slot == PERSIST_SLOTS - 1) ? 0 : slot + 1;
-            if (done) return;
+            if (done) {
+                finish();
+                return;
+            }
+            signal();
         }
     }
 
     if (threadIdx.x >= THREADS) {
         // ================================================================ producer warp (lane 0)
+        // Stages each tile as the per-pass kernel does, and records its pair
+        // counter in the signal ring (at most PERSIST_PEND tiles ahead of the
+        // tiles counted done).
         if (threadIdx.x != THREADS) return;
         int slot = 0;
         uint32_t sph = 0;
-        int64_t it = 0;
+        int64_t it = 0;        // stage uses so far
+        unsigned issued = 0;   // tiles staged
         int stg = 0;
         uint32_t ph = 0;
         auto drain = [&]() {  // wait (bounded) for this CTA's copies still in flight
             for (int64_t jt = (it > STAGES ? it - STAGES : 0); jt < it; ++jt)
                 mbar_wait(&full[jt % STAGES], (uint32_t)((jt / STAGES) & 1), WAIT_LIMIT);
         };
+        auto fail = [&]() {
+            if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
+            drain();
+        };
         auto claim = [&]() -> bool {  // the next stage is free
             if (it >= STAGES && !mbar_wait(&empty[stg], ph ^ 1u, WAIT_LIMIT)) {
-                if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
-                drain();
+                fail();
                 return false;
             }
+            return true;
+        };
+        auto ring_room = [&]() -> bool {  // the signal ring has a free entry
+            if (issued - ld_acquire_cta(&ring->retired) < (unsigned)PERSIST_PEND) return true;
+            const uint64_t t0 = global_ns();
+            for (uint32_t i = 1; issued - ld_acquire_cta(&ring->retired) >= (unsigned)PERSIST_PEND; ++i)
+                if ((i & 63) == 0 && global_ns() - t0 > WAIT_LIMIT) {
+                    fail();
+                    return false;
+                }
             return true;
         };
         auto advance = [&]() {
@@ -423,26 +533,29 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
         };
         for (;;) {
             if (!mbar_wait(&sfull[slot], sph, WAIT_LIMIT)) {
-                if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
-                drain();
-                return;
+                fail();
+                break;
             }
             const BatchSlot &bs = slots[slot];
             if (bs.count < 0) {
                 // tell the consumers there is no more work
-                if (!claim()) return;
+                if (!claim()) break;
                 StageDesc d{};
                 d.flags = STAGE_STOP;
                 *stage_desc(stg) = d;
                 mbar_arrive_expect_tx(&full[stg], 0);
                 advance();
                 drain();
-                return;
+                break;
             }
-            for (int u = 0; u < bs.count; ++u) {
+            bool ok = true;
+            for (int u = 0; u < bs.count && ok; ++u) {
                 const BatchRec r = bs.rec[u];
                 if (!(r.flags & 1)) continue;
-                if (!claim()) return;
+                if (!claim() || !ring_room()) {
+                    ok = false;
+                    break;
+                }
                 if (!(g.withhold && blockIdx.x == 0 && it == 0)) {  // test hook: nothing arrives
                     // the consumers' reads of this stage, and (through the search
                     // warp's acquire) other CTAs' stores of the runs, before the copies
@@ -451,30 +564,34 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                     const int s = stg;
                     const K *src = (r.flags & 2) ? buf_k1 : buf_k0;
                     StageDesc d{};
-                    uint32_t issued = 0;
+                    uint32_t tx = 0;
                     d.o_lo = r.x0;
                     d.na = (int)(r.a_hi - r.a_lo);
                     d.nb = (int)(r.b_hi - r.b_lo);
                     d.flags = 1 | (((r.flags >> 2) & 1) << 1) | ((r.flags & 8) ? 4 : 0);
-                    d.ctr = r.ctr;
                     const int ak = window_span<K>(r.a_lo, r.a_hi);
-                    d.a_off = stage_window_cg(stage_k(s), src, n, r.a_lo, r.a_hi, &full[s], &issued);
-                    d.b_off = ak + stage_window_cg(stage_k(s) + ak, src, n, r.b_lo, r.b_hi, &full[s], &issued);
+                    d.a_off = stage_window_cg(stage_k(s), src, n, r.a_lo, r.a_hi, &full[s], &tx);
+                    d.b_off = ak + stage_window_cg(stage_k(s) + ak, src, n, r.b_lo, r.b_hi, &full[s], &tx);
                     if constexpr (HV) {
                         const V *srcv = (r.flags & 2) ? buf_v1 : buf_v0;
                         const int av = window_span<V>(r.a_lo, r.a_hi);
-                        d.av_off = stage_window_cg(stage_v(s), srcv, n, r.a_lo, r.a_hi, &full[s], &issued);
-                        d.bv_off = av + stage_window_cg(stage_v(s) + av, srcv, n, r.b_lo, r.b_hi, &full[s], &issued);
+                        d.av_off = stage_window_cg(stage_v(s), srcv, n, r.a_lo, r.a_hi, &full[s], &tx);
+                        d.bv_off = av + stage_window_cg(stage_v(s) + av, srcv, n, r.b_lo, r.b_hi, &full[s], &tx);
                     }
                     *stage_desc(s) = d;
-                    mbar_arrive_expect_tx(&full[s], issued);
+                    ring->ctr[issued % PERSIST_PEND] = r.ctr;  // published by the arrive below
+                    ++issued;
+                    mbar_arrive_expect_tx(&full[s], tx);
                 }
                 advance();
             }
+            if (!ok) break;
             mbar_arrive(&sempty[slot]);
             sph ^= (slot == PERSIST_SLOTS - 1);
             slot = (slot == PERSIST_SLOTS - 1) ? 0 : slot + 1;
         }
+        st_release_cta(&ring->final_tiles, issued);  // the search warp may finish counting
+        return;
     }
 
     // ==================================================================== consumers
@@ -499,13 +616,10 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
         thread_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv, d.o_lo,
                                     fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),
                                     reinterpret_cast<uint32_t *>(ws + WS::keys));
-        // count this warp's part of the tile done: its stores, then a release
+        // this warp's part of the tile is stored (release at CTA scope); the
+        // search warp counts the tile done once every consumer warp has said so
         __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            fence_proxy_async_global();
-            atomicAdd(d.ctr, 1u);
-        }
+        if (lane == 0) red_release_cta_add(&ring->done[tid >> 5], 1u);
         if (tid == 0) count_bytes(g, CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * (na + nb));
     }
 }
