@@ -68,8 +68,8 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
-    ap.add_argument("--tile-log2", type=int, default=12,
-                    help="sort-phase tile 2^k keys (the bench default: 4096-key sort and merge tiles)")
+    ap.add_argument("--tile-log2", type=int, default=13,
+                    help="sort-phase tile 2^k keys (the bench default: 8192-key sort and merge tiles)")
     ap.add_argument("--merge", choices=["auto", "simple", "tma"], default="auto",
                     help="merge-pass kernel (auto: TMA pipeline where it fits)")
     ap.add_argument("--e2e-steps", type=int, default=20)

@@ -37,6 +37,15 @@ __global__ void balanced_offsets_kernel(int64_t *off, int64_t n, int64_t p) {
     }
 }
 
+// Zeroes n 32-bit words (the persistent merge's queue head and pair
+// counters).  A kernel rather than cudaMemsetAsync: a memset may be carried
+// out by a copy engine, and would then queue behind large host copies.
+__global__ void zero_words_kernel(unsigned *p, int64_t n) {
+    griddep_wait();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
 // Caller offsets must start at 0, end at n, never decrease, and (when a
 // bound is given) hold no segment longer than max_len.
 __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n, int64_t max_len,
@@ -396,9 +405,12 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     }
     const bool persist = h->persistent && !oddeven;
     const int64_t pwords = persist_words((int)Lmax0, ub0, g.R, blocks);
-    if (persist && pwords <= W.pcnt_words &&
-        cudaMemsetAsync(ws + W.pcnt, 0, (size_t)pwords * 4, stream) != cudaSuccess)
-        return BS_ERR_CUDA;
+    if (persist && pwords <= W.pcnt_words) {
+        launch_begin(h, CLS_SETUP, stream);
+        launch_overlapped(zero_words_kernel, blocks_for(pwords, 256, h->sms * 8), 256, 0, stream,
+                          (unsigned *)(ws + W.pcnt), pwords);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    }
     if (oddeven) {
         // scatter + encode into the padded buffer A; then sort A in place
         void *A = ws + W.total;
@@ -692,7 +704,12 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
         return BS_ERR_CUDA;
     const int64_t pwords = persist_words(0, 0, R, runs);
     const bool persist = h->persistent && pwords <= W.pcnt_words;
-    if (persist && cudaMemsetAsync(ws + W.pcnt, 0, (size_t)pwords * 4, s) != cudaSuccess) return BS_ERR_CUDA;
+    if (persist) {
+        launch_begin(h, CLS_SETUP, s);
+        launch_overlapped(zero_words_kernel, blocks_for(pwords, 256, h->sms * 8), 256, 0, s,
+                          (unsigned *)(ws + W.pcnt), pwords);
+        if (!launch_end(h, CLS_SETUP, s)) return BS_ERR_CUDA;
+    }
     Geo g{};
     g.off = off;
     g.S = runs;

@@ -1460,11 +1460,16 @@ __device__ __forceinline__ void warp_merge_tile(const K *sa, const K *sb, const 
 // first writes the largest key just past B's last item (stage slack, past
 // what the copies delivered), so an exhausted B never wins; A's end is
 // tested explicitly.
-template <class K, class V, int VT>
+// A hook that does nothing (thread_merge_tile's default before_store).
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <class K, class V, int VT, class Hook = NoHook>
 __device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *sav, const V *sbv,
                                                   int na, int nb, K *dk, V *dv, int64_t o_lo, bool fin,
                                                   int codec, uint64_t *empty_bar, int tid, K *wk,
-                                                  uint32_t *wx) {
+                                                  uint32_t *wx, Hook before_store = Hook()) {
     constexpr bool HV = HasVal<V>::value;
     constexpr int WO = 32 * VT;
     const int lane = tid & 31, w = tid >> 5;
@@ -1486,6 +1491,7 @@ __device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *s
         const bool all_a = wn > 0 && i0 + wn <= na && (j0 >= nb || !(sb[j0] < sa[i0 + wn - 1]));
         const bool all_b = wn > 0 && !all_a && j0 + wn <= nb && (i0 >= na || sb[j0 + wn - 1] < sa[i0]);
         if (all_a || all_b) {
+            before_store();
             const K *src = all_a ? sa + i0 : sb + j0;
             const V *srcv = all_a ? sav + i0 : sbv + j0;
             K *out = dk + o_lo + d0;
@@ -1524,6 +1530,7 @@ __device__ __forceinline__ void thread_merge_tile(const K *sa, K *sb, const V *s
         b = tb ? nxt : b;
     }
     if constexpr (!HV) mbar_arrive(empty_bar);  // every shared read of this stage is done
+    before_store();
     if constexpr (S == VT)
         store_warp_outputs<K, V, VT>(v, x, sav, sbv, na, dk, dv, o_lo + d0, d1 - d0, fin, codec, empty_bar, lane,
                                      wk, wx);

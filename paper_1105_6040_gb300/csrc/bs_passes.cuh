@@ -166,10 +166,17 @@ int launch_merge_persist_at(const PassArgs &a, Launcher &L, const PersistPlan &P
     constexpr size_t smem = persist_smem_bytes<K, V, MT, MVT, MERGE_STAGES>();
     static std::atomic<int> occ{0};
     if (!occ.load()) {
-        if (smem <= SMEM_OPT_IN_LIMIT && allow_smem(kern, smem))
-            occ.store(resident_ctas(kern, persist_block<MT>(), smem));
-        else
-            occ.store(-1);
+        int o = -1;
+        if (smem <= SMEM_OPT_IN_LIMIT && allow_smem(kern, smem)) {
+            o = resident_ctas(kern, persist_block<MT>(), smem);
+            // the merge is latency-bound: fewer resident CTAs than the per-pass
+            // TMA kernel would have costs more than the launches it saves
+            auto mt = merge_tma_kernel<K, V, MT, MVT, MERGE_STAGES, false>;
+            constexpr size_t msmem = tma_smem_bytes<K, V, MT, MVT, MERGE_STAGES, true>();
+            if (msmem <= SMEM_OPT_IN_LIMIT && allow_smem(mt, msmem) && resident_ctas(mt, MT + 32, msmem) > o)
+                o = -1;
+        }
+        occ.store(o);
     }
     if (occ.load() <= 0) return 0;
     if (a.merge_impl == MERGE_AUTO && smem > TMA_SMEM_AUTO_LIMIT) return 0;

@@ -199,12 +199,14 @@ __device__ __forceinline__ bool deps_done(const PairDeps &d) {
     return (!d.dep0 || ld_acquire_u32(d.dep0) >= d.need0) && (!d.dep1 || ld_acquire_u32(d.dep1) >= d.need1);
 }
 
-// One tile's slices as the search warp hands them to the producer.
+// One tile's slices as the search warp hands them to the producer (kept
+// small: the slots' shared memory decides whether a third CTA fits per SM for
+// wide items).
 struct BatchRec {
-    int64_t a_lo, a_hi, b_lo, b_hi, x0;
-    unsigned *ctr;
-    int flags;  // bit0 active, bit1 src parity, bit2 dst parity, bit3 final pass
-    int pad;
+    int64_t a_lo, b_lo, x0;
+    int na, nb;
+    unsigned ctr;  // its pair counter: cnt_seg + ctr
+    int flags;     // bit0 active, bit1 src parity, bit2 dst parity, bit3 final pass
 };
 struct BatchSlot {
     BatchRec rec[PERSIST_BATCH];
@@ -218,7 +220,7 @@ constexpr int PERSIST_PEND = 32;  // tiles staged but not yet counted done, at m
 
 // Shared state between the consumers, the producer and the signal thread.
 struct SignalRing {
-    unsigned *ctr[PERSIST_PEND];  // pair counter of staged tile j, at j % PERSIST_PEND
+    unsigned ctr[PERSIST_PEND];   // pair counter of staged tile j (cnt_seg + ctr), at j % PERSIST_PEND
     unsigned done[32];            // tiles consumer warp w has stored (monotone)
     unsigned retired;             // tiles counted done
     unsigned final_tiles;         // tiles staged in all, once the producer stops (~0u before)
@@ -333,7 +335,7 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                 if (m != retired) {
                     __threadfence();
                     fence_proxy_async_global();
-                    for (; retired != m; ++retired) atomicAdd(ring->ctr[retired % PERSIST_PEND], 1u);
+                    for (; retired != m; ++retired) atomicAdd(P.cnt_seg + ring->ctr[retired % PERSIST_PEND], 1u);
                     st_release_cta(&ring->retired, retired);
                     any = true;
                 }
@@ -465,12 +467,13 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                     const int64_t len = p.x1 - p.x0;
                     r.a_lo = clamp64(s_lo, p.ps, p.pm);
                     const int64_t a_hi = (p.x1 == p.pe) ? p.pm : s_hi;
-                    r.a_hi = clamp64(a_hi, r.a_lo, min(p.pm, r.a_lo + len));
+                    const int64_t ahc = clamp64(a_hi, r.a_lo, min(p.pm, r.a_lo + len));
                     r.b_lo = clamp64(p.pm + (p.x0 - p.ps) - (r.a_lo - p.ps), p.pm, p.pe);
-                    const int64_t nbk = min(len - (r.a_hi - r.a_lo), p.pe - r.b_lo);
-                    r.b_hi = r.b_lo + (nbk > 0 ? nbk : 0);
+                    const int64_t nbk = min(len - (ahc - r.a_lo), p.pe - r.b_lo);
+                    r.na = (int)(ahc - r.a_lo);
+                    r.nb = (int)(nbk > 0 ? nbk : 0);
                     r.x0 = p.x0;
-                    r.ctr = dp.ctr;
+                    r.ctr = (unsigned)(dp.ctr - P.cnt_seg);
                     r.flags = 1 | (p.src << 1) | (p.dst << 2) | (p.fin ? 8 : 0);
                 }
                 bs.rec[lane] = r;
@@ -566,17 +569,18 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
                     StageDesc d{};
                     uint32_t tx = 0;
                     d.o_lo = r.x0;
-                    d.na = (int)(r.a_hi - r.a_lo);
-                    d.nb = (int)(r.b_hi - r.b_lo);
+                    d.na = r.na;
+                    d.nb = r.nb;
                     d.flags = 1 | (((r.flags >> 2) & 1) << 1) | ((r.flags & 8) ? 4 : 0);
-                    const int ak = window_span<K>(r.a_lo, r.a_hi);
-                    d.a_off = stage_window_cg(stage_k(s), src, n, r.a_lo, r.a_hi, &full[s], &tx);
-                    d.b_off = ak + stage_window_cg(stage_k(s) + ak, src, n, r.b_lo, r.b_hi, &full[s], &tx);
+                    const int64_t a_hi = r.a_lo + r.na, b_hi = r.b_lo + r.nb;
+                    const int ak = window_span<K>(r.a_lo, a_hi);
+                    d.a_off = stage_window_cg(stage_k(s), src, n, r.a_lo, a_hi, &full[s], &tx);
+                    d.b_off = ak + stage_window_cg(stage_k(s) + ak, src, n, r.b_lo, b_hi, &full[s], &tx);
                     if constexpr (HV) {
                         const V *srcv = (r.flags & 2) ? buf_v1 : buf_v0;
-                        const int av = window_span<V>(r.a_lo, r.a_hi);
-                        d.av_off = stage_window_cg(stage_v(s), srcv, n, r.a_lo, r.a_hi, &full[s], &tx);
-                        d.bv_off = av + stage_window_cg(stage_v(s) + av, srcv, n, r.b_lo, r.b_hi, &full[s], &tx);
+                        const int av = window_span<V>(r.a_lo, a_hi);
+                        d.av_off = stage_window_cg(stage_v(s), srcv, n, r.a_lo, a_hi, &full[s], &tx);
+                        d.bv_off = av + stage_window_cg(stage_v(s) + av, srcv, n, r.b_lo, b_hi, &full[s], &tx);
                     }
                     *stage_desc(s) = d;
                     ring->ctr[issued % PERSIST_PEND] = r.ctr;  // published by the arrive below
@@ -598,14 +602,30 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
     const int tid = threadIdx.x, lane = tid & 31;
     int stg = 0;
     uint32_t ph = 0;
+    // A warp counts its part of a tile stored (release at CTA scope) just
+    // before it stores the next tile, or before it waits for one: the release
+    // then finds the tile's stores long complete instead of waiting for them.
+    bool pend = false;
+    unsigned *my_done = &ring->done[tid >> 5];
+    auto release_prev = [&]() {
+        if (pend) {
+            __syncwarp();
+            if (lane == 0) red_release_cta_add(my_done, 1u);
+            pend = false;
+        }
+    };
     for (;; ph ^= (stg == STAGES - 1), stg = (stg == STAGES - 1) ? 0 : stg + 1) {
         const int s = stg;
+        if (pend && !mbar_try_wait(&full[s], ph)) release_prev();  // about to wait
         if (!mbar_wait(&full[s], ph, WAIT_LIMIT)) {
             if (g.err) atomicCAS(g.err, 0, (int)BS_ERR_TIMEOUT);
             return;
         }
         const StageDesc d = *stage_desc(s);
-        if (d.flags & STAGE_STOP) return;
+        if (d.flags & STAGE_STOP) {
+            release_prev();
+            return;
+        }
         const K *sa = stage_k(s) + d.a_off;
         K *sb = stage_k(s) + d.b_off;
         const int na = d.na, nb = d.nb;
@@ -615,11 +635,10 @@ merge_persist_kernel(Geo g, const __grid_constant__ PersistPlan P, K *buf_k0, K 
         V *dv = out_buf<V>(fin, g.fin_v, (d.flags >> 1) & 1, buf_v0, buf_v1);
         thread_merge_tile<K, V, VT>(sa, sb, stage_v(s) + d.av_off, stage_v(s) + d.bv_off, na, nb, dk, dv, d.o_lo,
                                     fin, codec, &empty[s], tid, reinterpret_cast<K *>(ws),
-                                    reinterpret_cast<uint32_t *>(ws + WS::keys));
-        // this warp's part of the tile is stored (release at CTA scope); the
-        // search warp counts the tile done once every consumer warp has said so
-        __syncwarp();
-        if (lane == 0) red_release_cta_add(&ring->done[tid >> 5], 1u);
+                                    reinterpret_cast<uint32_t *>(ws + WS::keys), release_prev);
+        // this warp's part of the tile is stored; it says so later (release_prev),
+        // and the search warp counts the tile done once every consumer warp has
+        pend = true;
         if (tid == 0) count_bytes(g, CLS_MERGE, 2ull * (sizeof(K) + (HV ? sizeof(V) : 0)) * (na + nb));
     }
 }
