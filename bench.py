@@ -74,6 +74,10 @@ def parse_args():
                     help="merge-pass kernel (auto: TMA pipeline where it fits)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra records of the default run (batched, pairs, serving)")
+    ap.add_argument("--serving-extra-s", type=float, default=10.0,
+                    help="seconds of arrivals in the default run's serving record")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
     return ap.parse_args()
 
@@ -274,6 +278,42 @@ def pass_counts(kernels, bytes_per_pass):
     return per_step / bytes_per_pass, merge_per_launch, name
 
 
+def extra_records(args):
+    """The records of the default run besides the headline: batched segmented
+    sorts (lengths log-uniform in [16, 2^17] -- about 2^28 keys -- and in
+    [16, 2^20] as the workload states it, about 1.9e9 keys) against one call per
+    array, 2^27 stable uint64+int32 pairs, and a short serving run.  Inputs
+    are made on the GPU by the seeded generators (the same bits as the host
+    ones)."""
+    import argparse as _ap
+    import torch
+    out = {}
+
+    def sub(**kw):
+        a = _ap.Namespace(**vars(args))
+        a.device_gen = True
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    def keep(rec, keys):
+        return {k: rec[k] for k in keys if k in rec}
+
+    common = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "clocks")
+    for name, hi in (("batched_2e17", 17), ("batched_2e20", 20)):
+        rec = run_batched(sub(seg_hi_log2=hi, steps=5 if hi == 17 else 3, warmup=2,
+                              per_array_rounds=1))
+        out[name] = keep(rec, common + ("per_array", "speedup_vs_per_array", "kernels_one_run"))
+        torch.cuda.empty_cache()
+    rec = run_pairs(sub(pairs_log2n=27, pairs_dist="uniform", steps=5, warmup=2, p=2))
+    out["pairs"] = keep(rec, common + ("roofline", "kernels", "checked"))
+    torch.cuda.empty_cache()
+    rec = run_serving(sub(duration=args.serving_extra_s))
+    out["serving"] = keep(rec, common + ("p50_ms", "p99_ms", "serving", "offered_gkeys_per_s"))
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -428,6 +468,13 @@ def run_ours(args):
     del d_in, d_out
     torch.cuda.empty_cache()
 
+    # ---- the metric's other clauses, each measured in this same run with its own
+    # clock samples (N = 1 only): batched vs per-array at both segment-length
+    # ranges, the stable pairs workload, and a short serving run (p50/p99)
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = extra_records(args)
+
     # ---- CPU baseline: the oracle on this host's cores, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -445,6 +492,8 @@ def run_ours(args):
             "gpu_launches": launches, "launches_per_step": launches / args.steps,
             "clocks": clk, "kernels": kernels,
         }
+        if extras is not None:
+            line["extras"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -465,12 +514,16 @@ def run_pairs(args):
     from paper_1105_6040_gb300 import workloads as W
 
     n = 1 << args.pairs_log2n
-    keys_h = (W.uniform_uint64(n, seed=SEED) if args.pairs_dist == "uniform"
-              else W.zipf_uint64(n, seed=SEED))
-    vals_h = W.index_payload(n)
     sorter = abi.Sorter(0, tile_log2=args.pairs_tile_log2, merge_kernel=args.merge, merge_vt=args.merge_vt,
                         merge_consumer=args.merge_consumer)  # merge tile: the library's choice
-    dk, dv = torch.from_numpy(keys_h).cuda(), torch.from_numpy(vals_h).cuda()
+    if getattr(args, "device_gen", False) and args.pairs_dist == "uniform":
+        dk = W.uniform_uint64_torch(n, seed=SEED).view(torch.uint64)  # the same bits, made on the GPU
+        dv = torch.arange(n, dtype=torch.int32, device="cuda")
+    else:
+        keys_h = (W.uniform_uint64(n, seed=SEED) if args.pairs_dist == "uniform"
+                  else W.zipf_uint64(n, seed=SEED))
+        vals_h = W.index_payload(n)
+        dk, dv = torch.from_numpy(keys_h).cuda(), torch.from_numpy(vals_h).cuda()
     ko, vo = torch.empty_like(dk), torch.empty_like(dv)
     stream = torch.cuda.current_stream()
 
@@ -544,8 +597,7 @@ def run_pairs(args):
         "checked": "payload permutation, keys carried with payloads, nondecreasing, stable",
     }
     sorter.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------- batched workload
@@ -567,8 +619,10 @@ def run_batched(args):
     lens = W.loguniform_lengths(args.segments, args.seg_lo, hi, seed=SEED)
     off = W.offsets_from_lengths(lens)
     n = int(off[-1])
-    keys = W.uniform_int32(n, seed=SEED)
-    d_in = torch.from_numpy(keys).cuda()
+    if getattr(args, "device_gen", False):
+        d_in = W.uniform_int32_torch(n, seed=SEED)  # the same bits, made on the GPU
+    else:
+        d_in = torch.from_numpy(W.uniform_int32(n, seed=SEED)).cuda()
     d_out = torch.empty_like(d_in)
     d_off = torch.from_numpy(off).cuda()
     sorter = abi.Sorter(local)
@@ -656,8 +710,7 @@ def run_batched(args):
         "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s",
                      "peak_source": f"{peak_src} (copy bandwidth)"},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------- serving workload
@@ -690,8 +743,7 @@ def run_serving(args):
         "serving": summary, "clocks": clk,
         "offered_gkeys_per_s": sum(r.n for r in reqs) / cfg.duration / 1e9,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------- p sweep (Table 1 analogue)
@@ -828,18 +880,16 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "serving":
-        return run_serving(args)
+    if args.workload in ("batched", "serving", "pairs"):
+        fn = {"batched": run_batched, "serving": run_serving, "pairs": run_pairs}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return 0
     if args.workload == "memory":
         return run_memory(args)
     if args.workload == "psweep":
         return run_psweep(args)
     if args.workload == "localsort":
         return run_localsort(args)
-    if args.workload == "pairs":
-        return run_pairs(args)
     return run_ours(args)
 
 

@@ -86,6 +86,54 @@ def uniform_int32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     return out
 
 
+def _s64(u: int) -> int:
+    """A 64-bit pattern as the signed value torch's int64 holds."""
+    u &= 0xFFFFFFFFFFFFFFFF
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _mix_t(z):
+    """splitmix64's finaliser on a torch int64 tensor (wrapping arithmetic,
+    logical right shifts)."""
+    def shr(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+    z = (z ^ shr(z, 30)) * _s64(int(_M1))
+    z = (z ^ shr(z, 27)) * _s64(int(_M2))
+    return z ^ shr(z, 31)
+
+
+def splitmix64_torch(seed: int, start: int, count: int, device="cuda"):
+    """The same stream as splitmix64(), as the bits of a torch int64 tensor
+    generated on `device` (for inputs too large to generate on the host)."""
+    import torch
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    s = _s64(seed)
+    g = _s64(int(GOLDEN))
+    chunk = 1 << 26
+    for c0 in range(0, count, chunk):
+        c1 = min(count, c0 + chunk)
+        i = torch.arange(start + c0 + 1, start + c1 + 1, dtype=torch.int64, device=device)
+        out[c0:c1] = _mix_t(i * g + s)
+    return out
+
+
+def uniform_int32_torch(n: int, seed: int = DEFAULT_SEED, device="cuda"):
+    """uniform_int32(n, seed), generated on `device` as a torch int32 tensor."""
+    import torch
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    chunk = 1 << 26
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        h = splitmix64_torch(seed ^ STREAM_KEYS, c0, c1 - c0, device)
+        out[c0:c1] = (h & 0xFFFFFFFF).to(torch.int32)  # low 32 bits, wrapped
+    return out
+
+
+def uniform_uint64_torch(n: int, seed: int = DEFAULT_SEED, device="cuda"):
+    """uniform_uint64(n, seed), generated on `device` (bits in a torch int64 tensor)."""
+    return splitmix64_torch(seed ^ STREAM_KEYS, 0, n, device)
+
+
 def sorted_int32(n: int) -> np.ndarray:
     """a_i = INT32_MIN + floor(i * 2^32 / n): strictly increasing for n <= 2^32."""
     if n == 0:

@@ -452,8 +452,9 @@ def test_pairs_uint64_int32_full_size(sorter, dist, log2n):
     """The stable-pairs workload at full size (Zipf at 2^26 to bound the host
     generator's time): the output is the stable sort iff the payload is a
     permutation, every key travelled with its payload, the keys are
-    nondecreasing and equal keys keep their payload order; sampled ranks are
-    computed by the oracle."""
+    nondecreasing and equal keys keep their payload order (fast checks on the
+    GPU); then keys and values are compared element by element with the
+    oracle's stable sort."""
     n = 1 << log2n
     k = W.uniform_uint64(n, seed=W.DEFAULT_SEED) if dist == "uniform" else W.zipf_uint64(n, seed=W.DEFAULT_SEED)
     v = W.index_payload(n)
@@ -467,23 +468,32 @@ def test_pairs_uint64_int32_full_size(sorter, dist, log2n):
     assert bool((code[1:] >= code[:-1]).all())
     eq = code[1:] == code[:-1]
     assert bool((vo[1:][eq] > vo[:-1][eq]).all())
-    got = _to_host(ko)
+    got_k, got_v = _to_host(ko), _to_host(vo)
     del dk, dv, ko, vo, idx, code, eq
     torch.cuda.empty_cache()
-    rng = np.random.default_rng(1)
-    for i in np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 13)]):
-        lt, le = oracle.rank_bounds(k, int(got[i]))
-        assert lt <= i < le, i
+    # element by element against the oracle (its output does not depend on p,
+    # which its pins fix, so it runs one block per host core)
+    cores = os.cpu_count() or 1
+    wk, wv = oracle.sort(k, v, p=cores, threads=cores)
+    assert np.array_equal(got_k, wk)
+    assert np.array_equal(got_v, wv)
 
 
-def test_2e28_int32_uniform_p2_sampled(sorter):
-    """The benchmark's workload: 2^28 uniform int32 keys, p = 2.  Checked by
-    properties that hold at any size plus sampled ranks computed by the oracle."""
+def test_2e28_int32_uniform_p2_full_compare(sorter):
+    """The benchmark's workload: 2^28 uniform int32 keys, p = 2, in the
+    benchmark's launch configuration (8192-key tiles).  Fast checks first
+    (nondecreasing, two multiset hashes, sampled oracle ranks), then the whole
+    output element by element against the oracle."""
+    from paper_1105_6040_gb300.abi import Sorter
     n = 1 << 28
     x = W.uniform_int32(n, seed=W.DEFAULT_SEED)
     xt = _to_dev(x)
-    out = sorter.sort_keys(xt, p=2)
-    sorter.sync()
+    s13 = Sorter(0, tile_log2=13)
+    try:
+        out = s13.sort_keys(xt, p=2)
+        s13.sync()
+    finally:
+        s13.close()
     got = _to_host(out)
     del xt, out
     torch.cuda.empty_cache()
@@ -495,6 +505,12 @@ def test_2e28_int32_uniform_p2_sampled(sorter):
     for k in np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 13)]):
         lt, le = oracle.rank_bounds(cin, int(cout[k]))
         assert lt <= k < le, k
+    del cin, cout
+    # element by element against the oracle (one block per host core: its
+    # output does not depend on p, which its pins fix)
+    cores = os.cpu_count() or 1
+    want, _ = oracle.sort(x, p=cores, threads=cores)
+    assert np.array_equal(got, want)
 
 
 # ------------------------------------------------------------------ merge kernels
