@@ -118,7 +118,8 @@ def traffic_from_profiles(kernel: str, workload: str):
     if not os.path.isdir(pdir):
         return None
     digest = kernel_digest()
-    pat = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+sources=(\w+)")
+    pat = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)"
+                     r"(?:\s+passes=\d+)?\s+sources=(\w+)")
     for name in sorted(os.listdir(pdir)):
         if not name.endswith((".md", ".txt")):
             continue

@@ -7,7 +7,8 @@ import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PROFILES = os.path.join(ROOT, "profiles")
-TRAFFIC = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+sources=(\w+)")
+TRAFFIC = re.compile(r"traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)"
+                     r"(?:\s+passes=(\d+))?\s+sources=(\w+)")
 
 
 def _bench():
@@ -37,12 +38,14 @@ def test_traffic_records_parse_and_are_plausible():
     for name in _summaries():
         for m in TRAFFIC.finditer(open(os.path.join(PROFILES, name)).read()):
             found += 1
-            kernel, workload, nbytes, sources = m.groups()
+            kernel, workload, nbytes, passes, sources = m.groups()
             assert re.fullmatch(r"[0-9a-f]{16}", sources), (name, sources)
-            # one launch over 2^28 int32 keys moves 2 x 4 B x 2^28 algorithmic
-            # bytes; DRAM traffic within 10% of that (writes may stay in L2)
+            # one pass over 2^28 int32 keys moves 2 x 4 B x 2^28 algorithmic
+            # bytes (a persistent merge launch runs `passes` of them); DRAM
+            # traffic within 10% of that (writes may stay in L2)
             if workload.startswith("int32_2e28"):
-                assert 0.9 * 2 * 4 * 2**28 <= int(nbytes) <= 1.1 * 2 * 4 * 2**28, (name, nbytes)
+                per_pass = int(nbytes) / int(passes or 1)
+                assert 0.9 * 2 * 4 * 2**28 <= per_pass <= 1.1 * 2 * 4 * 2**28, (name, nbytes, passes)
     assert found >= 1
 
 
@@ -51,6 +54,7 @@ def test_benchmark_reads_a_record_only_for_matching_device_code():
     digest = bench.kernel_digest()
     recs = [m.groups() for name in _summaries()
             for m in TRAFFIC.finditer(open(os.path.join(PROFILES, name)).read())]
+    recs = [(k, w, b, src) for k, w, b, _, src in recs]
     for kernel, workload, nbytes, sources in recs:
         got = bench.traffic_from_profiles(kernel, workload)
         if sources == digest:
