@@ -193,6 +193,19 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
 bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes);
 
 /*
+ * Grow the handle's scratch now to what one sort of n keys (value type vt,
+ * BS_NONE for none) in S blocks or segments needs (bs_workspace_bytes), so
+ * that later calls of up to that size and block/segment count allocate
+ * nothing: a serving loop reserves its handles' scratch once, before it
+ * admits work against the memory left.  Waits for the handle's work first
+ * when the scratch has to grow.  *bytes (may be NULL) receives the handle's
+ * scratch size afterwards.  Errors: INVALID_ARG (h NULL, n < 0, S < 0),
+ * UNSUPPORTED_DTYPE, OUT_OF_MEMORY.
+ */
+bs_status bs_reserve_workspace(bs_handle *h, int64_t n, int64_t S, bs_dtype kt, bs_dtype vt,
+                               size_t *bytes);
+
+/*
  * Wait for the handle's last stream and for every copy out queued by
  * bs_sort_keys_host_async, then return the first error the GPU recorded
  * since the previous call (and clear it), else a pending CUDA error, else

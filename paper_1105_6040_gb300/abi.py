@@ -41,6 +41,7 @@ SIGNATURES = {
     "bs_sort_segmented_gather": ([_P, _P, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I64, _INT, _INT,
                                   _P], _INT),
     "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
+    "bs_reserve_workspace": ([_P, _I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
     "bs_sync_status": ([_P], _INT),
     "bs_status_str": ([_INT], C.c_char_p),
     "bs_launch_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double), _INT], _INT),
@@ -164,6 +165,15 @@ def bs_workspace_bytes(n, S, kt, vt="none") -> int:
     out = C.c_size_t()
     _check(load().bs_workspace_bytes(int(n), int(S), dtype_code(kt), dtype_code(vt), C.byref(out)),
            "bs_workspace_bytes")
+    return out.value
+
+
+def bs_reserve_workspace(h, n, S, kt, vt="none") -> int:
+    """Grow the handle's scratch now for a sort of n keys in S blocks or
+    segments; returns the handle's scratch bytes."""
+    out = C.c_size_t()
+    _check(load().bs_reserve_workspace(h, int(n), int(S), dtype_code(kt), dtype_code(vt), C.byref(out)),
+           "bs_reserve_workspace")
     return out.value
 
 

@@ -873,6 +873,16 @@ bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, siz
     return BS_OK;
 }
 
+bs_status bs_reserve_workspace(bs_handle *h, int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes) {
+    if (!h || n < 0 || S < 0) return BS_ERR_INVALID_ARG;
+    if (!key_width(kt) || (vt != BS_NONE && !value_width(vt))) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (S < 1) S = 1;
+    DevGuard dg(h->device);
+    const bs_status st = ensure_ws(h, ws_layout(n, S, (size_t)key_width(kt), (size_t)value_width(vt)).total);
+    if (bytes) *bytes = h->ws_bytes;
+    return st;
+}
+
 bs_status bs_sync_status(bs_handle *h) {
     if (!h) return BS_ERR_INVALID_ARG;
     DevGuard dg(h->device);

@@ -11,9 +11,14 @@ A single-threaded scheduler runs the loop:
   of the same dtype, up to a key and request budget, as ONE gathered
   segmented sort (bs_sort_segmented_gather: each segment reads its keys from
   its own place in the pool, so no gather copy is needed);
-* a launch is admitted only while the bytes held by work in flight stay under
-  the memory cap (by default 80% of the free HBM when the loop starts);
-  otherwise it waits for running work to finish;
+* every slot's library handle reserves its scratch once, at start-up
+  (bs_reserve_workspace: enough for the largest request or batch it may
+  run), so a launch allocates only its output; a launch is admitted only
+  while the output bytes held by work in flight stay under the memory cap (by
+  default 80% of the HBM still free once pools and scratch are in place);
+  otherwise it waits for running work to finish (a launch with nothing in
+  flight is always admitted, so one request over the cap cannot stall the
+  loop);
 * completions are detected by CUDA events; a request's latency is the time
   from its arrival to the end of its GPU work (both measured from one common
   origin: a start event recorded when the loop starts).
@@ -163,6 +168,7 @@ def summarize(reqs: list[Request], sched: Scheduler) -> dict:
         "mean_batch_requests": float(np.mean(sched.batch_sizes)) if sched.batch_sizes else 0.0,
         "deferrals": sched.deferrals, "peak_in_flight_bytes": sched.peak_bytes,
         "mem_cap_bytes": sched.cap,
+        "reserved_scratch_bytes": int(getattr(sched.ex, "reserved_bytes", 0)),
     }
 
 
@@ -172,7 +178,7 @@ class GpuExecutor:
     def __init__(self, cfg: ServingConfig, device: int = 0):
         import torch
 
-        from .abi import Sorter
+        from .abi import Sorter, bs_reserve_workspace
         self.torch = torch
         self.cfg = cfg
         self.dev = torch.device("cuda", device)
@@ -183,9 +189,15 @@ class GpuExecutor:
             "float32": torch.from_numpy(W.normal_float32_edges(n, seed=cfg.seed ^ 0x11)).to(self.dev),
         }
         self.slots = []
+        self.reserved_bytes = 0
+        # the largest call a slot makes: one request of up to hi keys, or a
+        # batch of up to batch_max_keys keys in up to batch_max_reqs segments
+        res_n = max(cfg.hi, cfg.batch_max_keys)
+        res_s = max(1, cfg.batch_max_reqs)
         for _ in range(cfg.streams):
-            self.slots.append({"stream": torch.cuda.Stream(self.dev), "sorter": Sorter(device),
-                               "busy": None})
+            sorter = Sorter(device)
+            self.reserved_bytes += bs_reserve_workspace(sorter.h, res_n, res_s, "int32")
+            self.slots.append({"stream": torch.cuda.Stream(self.dev), "sorter": sorter, "busy": None})
         self.start_event = None
 
     # -- executor interface
@@ -202,9 +214,16 @@ class GpuExecutor:
 
     @staticmethod
     def bytes_for(batch) -> int:
-        # the output buffer plus the sort's scratch copy and index arrays
+        # what a launch allocates: its output (4-byte keys) and, for a batch,
+        # the segment offsets and sources (the handles' scratch is reserved)
         keys = sum(r.n for r in batch)
-        return 2 * 4 * keys + 64 * len(batch) + (1 << 16)
+        return 4 * keys + (16 * (len(batch) + 1) if len(batch) > 1 else 0)
+
+    def scratch_bytes(self) -> int:
+        """The slots' handles' scratch now (unchanged from the reservation
+        unless a call needed more)."""
+        from .abi import bs_reserve_workspace
+        return sum(bs_reserve_workspace(s["sorter"].h, 0, 1, "int32") for s in self.slots)
 
     def launch(self, slot_id: int, batch: list[Request]):
         t = self.torch

@@ -65,3 +65,40 @@ def test_gathered_segments_match_oracle():
         assert bs_sync_status(s.h) == BS_ERR_INVALID_ARG
     finally:
         s.close()
+
+
+def test_tight_memory_cap_defers_and_is_respected():
+    """Admission by memory: with a cap of three largest launches' outputs and
+    requests arriving ten times faster, launches are deferred, the bytes in
+    flight never exceed the cap, the handles' scratch reserved at start-up is
+    all the library uses (it does not grow during the run), batching engages,
+    and every result is still the request sorted alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_6040_gb300 import serving as S
+    from paper_1105_6040_gb300.abi import Sorter
+
+    cap = 3 * 4 * (1 << 16)
+    cfg = S.ServingConfig(rate=20000, duration=0.1, lo=1 << 10, hi=1 << 16, small_max=1 << 12,
+                          batch_max_keys=1 << 16, batch_max_reqs=64, streams=4,
+                          pool_keys=1 << 18, mem_cap_bytes=cap, keep_results=True)
+    summary, reqs, ex = S.serve(cfg)
+    alone = Sorter(0)
+    try:
+        assert summary["mem_cap_bytes"] == cap
+        assert summary["deferrals"] > 0
+        assert 0 < summary["peak_in_flight_bytes"] <= cap
+        assert summary["mean_batch_requests"] > 1.0
+        assert ex.scratch_bytes() == summary["reserved_scratch_bytes"] > 0
+        for r in reqs:
+            assert r.done >= r.launched >= r.arrival
+            want = alone.sort_keys(ex.pools[r.dtype][r.src:r.src + r.n], p=1)
+            alone.sync()
+            assert torch.equal(r.result.view(torch.int32), want.view(torch.int32)), r.rid
+        for r in reqs[::53]:
+            x = ex.pools[r.dtype][r.src:r.src + r.n].cpu().numpy()
+            w, _ = oracle.sort(x, p=1)
+            assert np.array_equal(r.result.cpu().numpy().view(np.uint32), w.view(np.uint32))
+    finally:
+        alone.close()
+        ex.close()
