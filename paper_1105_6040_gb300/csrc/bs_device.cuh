@@ -418,24 +418,160 @@ __device__ __forceinline__ void seq_merge_carry(const K *sk, const uint32_t *sx,
 
 // Shared memory of the tile sort: codes, then (pairs) original positions and
 // values, each at a 16-byte boundary.
+// Keys alone: two ping-pong buffers of keys_round_buf(T) keys each (see
+// tile_smem_rounds).
+__host__ __device__ constexpr int keys_round_buf(int T) {
+    // T keys, the first round's padding (one slot per 32), a sentinel per pair
+    // of runs of at least 512 keys, slack; rounded to 16 bytes of 8-byte keys
+    return ((T + T / 32 + T / 512 + 64) + 1) & ~1;
+}
 template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
-    return smem_val_offset<K>(T) +
-           (sizeof(V) > 1 ? smem_val_offset<uint32_t>(T) + sizeof(V) * (size_t)spad_size<V>(T) : 0);
+    return sizeof(V) > 1 ? smem_val_offset<K>(T) + smem_val_offset<uint32_t>(T) + sizeof(V) * (size_t)spad_size<V>(T)
+                         : 2 * sizeof(K) * (size_t)keys_round_buf(T);
 }
 
-// Merge rounds of the keys-only tile sort done with register shuffles
-// inside a warp before the shared-memory rounds take over.
-#ifndef TILE_SHUFFLE_ROUNDS
-#define TILE_SHUFFLE_ROUNDS 5
-#endif
+// The shared-memory merge rounds of the keys-only tile sort.  On entry every
+// warp holds one sorted run of M0 = 32*KPT keys, lane l the keys
+// [KPT*l, KPT*l + KPT) of it; each round merges pairs of runs (m -> 2m) until
+// the tile is one run, and the function returns where it lies (plain layout,
+// T keys), after a barrier.
+//
+// Layout.  A round reads pair q of runs A = [0, m), B = [m, 2m) from a region
+// of its source buffer and writes the merged run to the destination buffer,
+// ping-pong: pair q of a round's input lies at q*(2m+1), A first, then B,
+// then one slot holding the largest code (B's sentinel).  The first round's
+// input comes from registers: element e of pair q is at q*R1 + e + e/32
+// (R1 = 2*M0 + 2*M0/32 + 1), so that the 32 lanes writing KPT consecutive keys
+// each hit distinct banks; its sentinel is the region's last slot.
+//
+// Merge.  Warp w produces the outputs [w*M0, (w+1)*M0) of the round (one run
+// of 2m >= 2*M0 holds them all); lane l produces S = KPT+1 of them from
+// w*M0 + S*l on (the last lanes fewer), so lanes that write their outputs in
+// step sit an odd distance apart, in distinct banks.  A lane finds its
+// merge-path split by a binary search, then merges sequentially: each step
+// takes B's head when A is exhausted or B's head is smaller (A wins ties:
+// keys alone, either is right), stores it, and loads the next key of that
+// run.  B's sentinel stops B without a test; A's end is tested, because
+// A's successor is B's first key.  Keys equal to the largest code need no
+// special case: B's sentinel then ties with A's head and A is taken.  A lane
+// never consumes more than the 2m - diag keys left in its pair, so no read
+// passes B's sentinel, whatever the keys.
+template <class K, int THREADS, int KPT>
+__device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, int tid) {
+    constexpr int T = THREADS * KPT;
+    constexpr int M0 = 32 * KPT;  // run length after the warp rounds
+    constexpr int WO = M0;        // outputs per warp per round
+    constexpr int S = KPT + 1;    // outputs per lane (odd)
+    constexpr int R1 = 2 * M0 + (2 * M0) / 32 + 1;
+    static_assert(T >= 2 * M0, "at least one shared-memory round");
+    const int lane = tid & 31, w = tid >> 5;
+    {
+        const int q = w >> 1, h = w & 1;
+        K *pr = x + q * R1;
+#pragma unroll
+        for (int u = 0; u < KPT; ++u) {
+            const int e = h * M0 + lane * KPT + u;
+            pr[e + (e >> 5)] = k[u];
+        }
+        if (h == 1 && lane == 0) pr[R1 - 1] = max_code<K>();
+    }
+    __syncthreads();
+    const int start = min(S * lane, WO), cnt = min(S, WO - start);
+    const K *src = x;
+    K *dst = y;
+#pragma unroll 1
+    for (int m = M0; 2 * m <= T; m *= 2) {
+        const bool first = (m == M0), last = (2 * m == T);
+        const int p = (w * WO) / (2 * m);      // output run = input pair
+        const int diag = (w * WO) % (2 * m) + start;
+        // where output e of run p goes: the last round's plain layout, or the
+        // next round's pair layout (and this run's half of that pair)
+        K *out = last ? dst + p * (2 * m) : dst + (p >> 1) * (4 * m + 1) + (p & 1) * (2 * m);
+        if (!last && (p & 1) && (w * WO) % (2 * m) + WO == 2 * m && lane == 31)
+            out[2 * m] = max_code<K>();  // the next round's B sentinel
+        out += diag;
+        if (first) {
+            const K *pb0 = src + p * R1;
+            auto at = [&](int e) { return pb0[e + (e >> 5)]; };
+            int lo = diag > m ? diag - m : 0, hi = diag < m ? diag : m;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (at(m + diag - 1 - mid) < at(mid)) hi = mid;
+                else lo = mid + 1;
+            }
+            int ia = lo, ib = m + diag - lo;
+            K a = at(ia), b = at(ib);
+            if (cnt == S) {
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+                    const bool tb = ia >= m || b < a;
+                    out[u] = tb ? b : a;
+                    ia += tb ? 0 : 1;
+                    ib += tb ? 1 : 0;
+                    const K nxt = at(tb ? ib : ia);
+                    a = tb ? a : nxt;
+                    b = tb ? nxt : b;
+                }
+            } else {
+                for (int u = 0; u < cnt; ++u) {
+                    const bool tb = ia >= m || b < a;
+                    out[u] = tb ? b : a;
+                    ia += tb ? 0 : 1;
+                    ib += tb ? 1 : 0;
+                    const K nxt = at(tb ? ib : ia);
+                    a = tb ? a : nxt;
+                    b = tb ? nxt : b;
+                }
+            }
+        } else {
+            const K *base = src + p * (2 * m + 1);
+            int lo = diag > m ? diag - m : 0, hi = diag < m ? diag : m;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (base[m + diag - 1 - mid] < base[mid]) hi = mid;
+                else lo = mid + 1;
+            }
+            const K *pa = base + lo, *pb = base + m + (diag - lo);
+            const K *const a_end = base + m;
+            K a = *pa, b = *pb;
+            if (cnt == S) {
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+                    const bool tb = pa >= a_end || b < a;
+                    out[u] = tb ? b : a;
+                    pa += tb ? 0 : 1;
+                    pb += tb ? 1 : 0;
+                    const K nxt = *(tb ? pb : pa);
+                    a = tb ? a : nxt;
+                    b = tb ? nxt : b;
+                }
+            } else {
+                for (int u = 0; u < cnt; ++u) {
+                    const bool tb = pa >= a_end || b < a;
+                    out[u] = tb ? b : a;
+                    pa += tb ? 0 : 1;
+                    pb += tb ? 1 : 0;
+                    const K nxt = *(tb ? pb : pa);
+                    a = tb ? a : nxt;
+                    b = tb ? nxt : b;
+                }
+            }
+        }
+        __syncthreads();
+        src = dst;
+        dst = (dst == y) ? x : y;
+    }
+    return src;
+}
 
 // Tile sort (the sort phase of Fig. 1 at CTA scale).  Tile t covers
 // keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
-// KPT keys in registers; keys-only tiles then merge pairs of lists with up
-// to TILE_SHUFFLE_ROUNDS warp-shuffle rounds, and the remaining rounds merge
-// through shared memory (merge-path split + sequential merge of KPT
-// outputs per thread); rounds whose lists live inside one warp synchronise
-// only that warp.  Pairs sort
+// KPT keys in registers; keys-only tiles then merge pairs of lists with five
+// warp-shuffle rounds (one sorted run of 32*KPT keys per warp) and the
+// remaining rounds in shared memory (tile_smem_rounds); pairs merge every
+// round through shared memory (merge-path split + sequential merge of KPT
+// outputs per thread; rounds whose lists live inside one warp synchronise
+// only that warp).  Pairs sort
 // (code, original position), which is the stable order; values move once,
 // at the final store.  The sorted tile is written -- decoded if this is the
 // segment's last pass -- to the buffer its merge schedule starts from.
@@ -509,16 +645,27 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
             reg_sort_keys<KPT>(k);
         }
 
-        int r0 = 0;
         if constexpr (!HV) {
             // the first merges inside a warp: register shuffles, no shared memory
             const int lane = tid & 31;
 #pragma unroll 1
-            for (; r0 < TILE_SHUFFLE_ROUNDS && (2 << r0) <= 32 && (KPT << r0) < T; ++r0)
-                warp_merge_round<KPT>(k, r0, lane);
+            for (int r = 0; r < 5; ++r) warp_merge_round<KPT>(k, r, lane);
+            // then the shared-memory rounds, and the coalesced striped store
+            const K *res = tile_smem_rounds<K, THREADS, KPT>(k, sk, sk + keys_round_buf(T), tid);
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int pos = tid + u * THREADS;
+                if (pos < cnt) {
+                    const K c = res[pos];
+                    dst_k[base + pos] = fin ? dec_code(c, codec) : c;
+                }
+            }
+            if (tid == 0) count_bytes(g, CLS_TILE_SORT, 2ull * sizeof(K) * cnt);
+            __syncthreads();  // the buffers are free for the next tile
+            continue;
         }
 #pragma unroll 1
-        for (int r = r0; (KPT << r) < T; ++r) {
+        for (int r = 0; (KPT << r) < T; ++r) {
             const bool warp_round = (2 << r) <= 32;  // both lists inside one warp
 #pragma unroll
             for (int u = 0; u < KPT; ++u) {
