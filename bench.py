@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "sorted", "reverse", "dup16"])
+    ap.add_argument("--dists", default="",
+                    help="psweep: comma-separated distributions (default: --dist)")
     ap.add_argument("--tile-log2", type=int, default=13,
                     help="sort-phase tile 2^k keys (the bench default: 8192-key sort and merge tiles)")
     ap.add_argument("--merge", choices=["auto", "simple", "tma"], default="auto",
@@ -750,46 +752,65 @@ def run_serving(args):
 # ---------------------------------------------------------------- p sweep (Table 1 analogue)
 
 def run_psweep(args):
-    """Time against the number of blocks p for both merge-phase schedules (the
-    pairwise tree and Fig. 1's odd-even compare-split), the GPU analogue of
-    the paper's Exp. 1 / Table 1; plus the tree up to p = 4096."""
+    """Time against the number of blocks p, the GPU analogue of the paper's
+    Exp. 1 / Table 1: for each key distribution, the pairwise tree (the
+    default path: 8192-key tiles, the persistent merge) at p = 1 .. 4096 and
+    Fig. 1's odd-even compare-split schedule at p = 1 .. 64, with the time of
+    each kernel class and the passes per sort."""
     import torch
 
     from paper_1105_6040_gb300 import abi
+    from paper_1105_6040_gb300 import workloads as W
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    args.tile_log2, args.merge_tile_log2 = 12, 0  # the 4096-key tile every row uses (for config())
     n = 1 << args.log2n
-    x = torch.from_numpy(make_keys(args, 0)).cuda()
-    out = torch.empty_like(x)
+    out = None
     rows = []
     stream = torch.cuda.current_stream()
-    for sched in ("tree", "oddeven"):
-        ps = [1 << i for i in range(13)] if sched == "tree" else [1, 2, 4, 8, 16, 32, 64]
-        s = abi.Sorter(local, tile_log2=12)  # the 4096-key tile every row of this table uses
-        abi.bs_set_option(s.h, "merge_schedule", sched)
-        for p in ps:
-            for _ in range(2):
+    dists = args.dists.split(",") if args.dists else [args.dist]
+    for dist in dists:
+        x = W.int32_keys_torch(dist, n, seed=SEED)
+        out = torch.empty_like(x)
+        for sched in ("tree", "oddeven"):
+            ps = [1 << i for i in range(13)] if sched == "tree" else [1, 2, 4, 8, 16, 32, 64]
+            s = abi.Sorter(local, tile_log2=args.tile_log2)
+            abi.bs_set_option(s.h, "merge_schedule", sched)
+            for p in ps:
+                for _ in range(2):
+                    s.sort_keys(x, out=out, p=p)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(2, min(args.steps, 10))
+                e0.record(stream)
+                for _ in range(reps):
+                    s.sort_keys(x, out=out, p=p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                # one more sort with per-launch events and counted bytes
+                s.stats(reset=True)
+                abi.bs_set_option(s.h, "count_bytes", 1)
+                s.set_timing(True)
                 s.sort_keys(x, out=out, p=p)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = max(2, min(args.steps, 10))
-            e0.record(stream)
-            for _ in range(reps):
-                s.sort_keys(x, out=out, p=p)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            counts, _ = s.stats(reset=True)
-            rows.append({"schedule": sched, "p": p, "ms": ms, "gkeys_per_s": n / (ms * 1e-3) / 1e9,
-                         "merge_passes_per_sort": counts["merge"] / (reps + 2)})
-        assert bool((out[1:] >= out[:-1]).all())
-        s.close()
-    line = {"metric": f"time vs p, 2^{args.log2n} {args.dist} int32 keys (Table 1 analogue)",
+                s.sync()
+                s.set_timing(False)
+                abi.bs_set_option(s.h, "count_bytes", 0)
+                kms, kn = s.kernel_times()
+                counts, byts = s.stats(reset=True)
+                rows.append({"dist": dist, "schedule": sched, "p": p, "ms": ms,
+                             "gkeys_per_s": n / (ms * 1e-3) / 1e9,
+                             "passes": (byts["tile_sort"] + byts["merge"]) / (2 * 4 * n),
+                             "launches": int(sum(counts.values())),
+                             "kernel_ms": {k: round(v, 4) for k, v in kms.items() if kn[k]}})
+            assert bool((out[1:] >= out[:-1]).all())
+            s.close()
+        del x, out
+        torch.cuda.empty_cache()
+    line = {"metric": f"time vs p, 2^{args.log2n} int32 keys (Table 1 analogue)",
             "value": min(r["ms"] for r in rows), "unit": "ms", "n_gpus": 1,
             "higher_is_better": False, "data": "synthetic", "rows": rows,
-            "config": config(args)}
+            "config": {**config(args), "dists": dists}}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -193,6 +193,19 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
 bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes);
 
 /*
+ * Order keys: d_out[i] (int64, device) receives, for key d_in[i] of dtype kt,
+ * a signed 64-bit integer whose order is this library's sort order (the
+ * key's order-preserving code: 4-byte codes zero-extended, 8-byte codes with
+ * the top bit flipped; floating point by IEEE 754 totalOrder).  Used to cut
+ * sorted runs at splitters in the library's order, as the multi-GPU exchange
+ * sort's bucketing does (the merge phase of Fig. 1 across processes).  Runs
+ * on the current device, asynchronously on `stream`; needs no handle and
+ * allocates nothing.  Errors: INVALID_ARG (n < 0, NULL pointer with n > 0),
+ * UNSUPPORTED_DTYPE, CUDA.
+ */
+bs_status bs_order_keys(const void *d_in, int64_t *d_out, int64_t n, bs_dtype kt, void *stream);
+
+/*
  * Grow the handle's scratch now to what one sort of n keys (value type vt,
  * BS_NONE for none) in S blocks or segments needs (bs_workspace_bytes), so
  * that later calls of up to that size and block/segment count allocate

@@ -42,6 +42,7 @@ SIGNATURES = {
                                   _P], _INT),
     "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
     "bs_reserve_workspace": ([_P, _I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
+    "bs_order_keys": ([_P, _P, _I64, _INT, _P], _INT),
     "bs_sync_status": ([_P], _INT),
     "bs_status_str": ([_INT], C.c_char_p),
     "bs_launch_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double), _INT], _INT),
@@ -175,6 +176,23 @@ def bs_reserve_workspace(h, n, S, kt, vt="none") -> int:
     _check(load().bs_reserve_workspace(h, int(n), int(S), dtype_code(kt), dtype_code(vt), C.byref(out)),
            "bs_reserve_workspace")
     return out.value
+
+
+def bs_order_keys(d_in, d_out, n, kt, stream=0) -> None:
+    """d_out (int64) <- keys' order-preserving codes as signed 64-bit integers."""
+    _check(load().bs_order_keys(d_in, d_out, int(n), dtype_code(kt), stream or None), "bs_order_keys")
+
+
+def order_keys(keys, stream=None):
+    """A torch int64 tensor whose order (signed) is the library's sort order of
+    `keys` (a CUDA tensor of a key dtype)."""
+    import torch
+    if not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+    bs_order_keys(keys.data_ptr(), out.data_ptr(), keys.numel(), keys.dtype,
+                  _stream_ptr(stream, keys.device))
+    return out
 
 
 def bs_sync_status(h) -> int:

@@ -46,6 +46,18 @@ __global__ void zero_words_kernel(unsigned *p, int64_t n) {
         p[i] = 0u;
 }
 
+// Order keys: the order-preserving code of every key as a signed 64-bit
+// integer -- 4-byte codes zero-extended, 8-byte codes with the top bit
+// flipped -- so that a signed comparison gives the sort order.
+template <class K>
+__global__ void order_keys_kernel(const K *__restrict__ in, int64_t *out, int64_t n, int codec) {
+    griddep_wait();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const K c = enc_code(in[i], codec);
+        out[i] = sizeof(K) == 4 ? (int64_t)(uint64_t)c : (int64_t)((uint64_t)c ^ 0x8000000000000000ull);
+    }
+}
+
 // Caller offsets must start at 0, end at n, never decrease, and (when a
 // bound is given) hold no segment longer than max_len.
 __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n, int64_t max_len,
@@ -871,6 +883,26 @@ bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, siz
     if (S < 1) S = 1;
     *bytes = ws_layout(n, S, (size_t)key_width(kt), (size_t)value_width(vt)).total;
     return BS_OK;
+}
+
+bs_status bs_order_keys(const void *d_in, int64_t *d_out, int64_t n, bs_dtype kt, void *stream) {
+    if (n < 0) return BS_ERR_INVALID_ARG;
+    const int kw = key_width(kt);
+    if (!kw) return BS_ERR_UNSUPPORTED_DTYPE;
+    if (n == 0) return BS_OK;
+    if (!d_in || !d_out) return BS_ERR_INVALID_ARG;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    const unsigned grid = blocks_for(n, 256, sms * 8);
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (kw == 4)
+        launch_overlapped(order_keys_kernel<uint32_t>, grid, 256, 0, s, (const uint32_t *)d_in, d_out, n, key_codec(kt));
+    else
+        launch_overlapped(order_keys_kernel<uint64_t>, grid, 256, 0, s, (const uint64_t *)d_in, d_out, n, key_codec(kt));
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
 bs_status bs_reserve_workspace(bs_handle *h, int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes) {

@@ -19,9 +19,15 @@ sorts its block, then the blocks are merged.  Across GPUs that becomes:
   whole.  This replaces the log2 G rounds of pairwise merges that Fig. 1
   would take across processes by a single all-to-all.
 
-Keys: integer dtypes, whose numeric order is the sort order.  The collective
-backend is whatever the process group uses (gloo for CPU tensors, NCCL for
-CUDA tensors).
+Keys: every dtype the library sorts.  Splitters are chosen, and sorted
+blocks cut at them, in the library's own order: on the GPU through its order
+keys (bs_order_keys: each key's order-preserving code as a signed 64-bit
+integer, so floating point is cut by IEEE 754 totalOrder, -0 before +0, NaNs
+by payload); host tensors of signed integer dtypes use their numeric order,
+other host dtypes need an ``order_keys`` function.  Collectives run on the
+process group's backend: with NCCL on the device tensors, with gloo through
+host copies (keys stay on the device for the sorts), so ranks that share one
+GPU can run the whole path, as the tests do.
 """
 from __future__ import annotations
 
@@ -54,6 +60,26 @@ def _gpu_merge_runs(x, offsets):
     return s.merge_runs(x.contiguous(), [int(o) for o in offsets])
 
 
+def _order_keys(x):
+    """int64 keys whose (signed) order is the library's sort order of x."""
+    import torch
+    if x.is_cuda:
+        from .abi import order_keys
+        return order_keys(x.contiguous())
+    if x.dtype in (torch.int8, torch.int16, torch.int32, torch.int64):
+        return x.to(torch.int64)  # numeric order is the sort order
+    raise ValueError(f"host tensors of dtype {x.dtype} need an order_keys function")
+
+
+def _comm(t, group):
+    """The tensor a collective of this group can take: gloo works on host
+    tensors only, so device tensors go through host memory."""
+    import torch.distributed as dist
+    if t.is_cuda and dist.get_backend(group) == "gloo":
+        return t.cpu()
+    return t
+
+
 _SORTERS = {}
 
 
@@ -66,25 +92,28 @@ def _sorter(device):
 
 
 def choose_splitters(sorted_local, group=None, samples_per_rank: int = 64, local_sort=None):
-    """G-1 splitters from evenly spaced samples of every rank's sorted block."""
+    """G-1 splitters from evenly spaced samples of every rank's sorted block
+    (keys of any ordered dtype: here, order keys)."""
     import torch
     import torch.distributed as dist
     G = dist.get_world_size(group)
     n = sorted_local.numel()
     s = samples_per_rank
+    dev = sorted_local.device
     if n > 0:
-        pos = torch.div((torch.arange(1, s + 1, device=sorted_local.device) * n), s + 1,
+        pos = torch.div((torch.arange(1, s + 1, device=dev) * n), s + 1,
                         rounding_mode="floor").clamp(max=n - 1)
         samp = sorted_local[pos]
-        cnt = torch.tensor([s], device=sorted_local.device)
+        cnt = torch.tensor([s], device=dev)
     else:
-        samp = torch.zeros(s, dtype=sorted_local.dtype, device=sorted_local.device)
-        cnt = torch.tensor([0], device=sorted_local.device)
+        samp = torch.zeros(s, dtype=sorted_local.dtype, device=dev)
+        cnt = torch.tensor([0], device=dev)
+    samp, cnt = _comm(samp, group), _comm(cnt, group)
     all_samp = [torch.empty_like(samp) for _ in range(G)]
     all_cnt = [torch.empty_like(cnt) for _ in range(G)]
     dist.all_gather(all_samp, samp, group=group)
     dist.all_gather(all_cnt, cnt, group=group)
-    pool = torch.cat([a[:int(c.item())] for a, c in zip(all_samp, all_cnt)])
+    pool = torch.cat([a[:int(c.item())] for a, c in zip(all_samp, all_cnt)]).to(dev)
     pool = (local_sort or _gpu_local_sort)(pool.contiguous())  # G * samples_per_rank keys
     if pool.numel() == 0:
         return pool
@@ -92,35 +121,44 @@ def choose_splitters(sorted_local, group=None, samples_per_rank: int = 64, local
     return pool[idx]
 
 
-def exchange_sort(local, group=None, local_sort=None, merge_runs=None,
+def exchange_sort(local, group=None, local_sort=None, merge_runs=None, order_keys=None,
                   samples_per_rank: int = 64):
     """Sort a block-distributed array with one all-to-all exchange.
 
-    local: this rank's keys (1-D tensor, CPU with gloo or CUDA with NCCL).
-    local_sort(x) -> sorted x; merge_runs(x, offsets) -> sorted x from sorted
-    runs (defaults: the library's bs_sort_keys / bs_merge_runs on the GPU).
-    Returns this rank's part of the sorted whole (rank order = key order)."""
+    local: this rank's keys (1-D tensor: on the GPU, or on the host with a
+    gloo group).  local_sort(x) -> sorted x; merge_runs(x, offsets) -> sorted
+    x from sorted runs; order_keys(x) -> int64 keys in x's sort order
+    (defaults: the library's bs_sort_keys, bs_merge_runs and bs_order_keys on
+    the GPU).  Returns this rank's part of the sorted whole (rank order = key
+    order)."""
     import torch
     import torch.distributed as dist
     local_sort = local_sort or _gpu_local_sort
     merge_runs = merge_runs or _gpu_merge_runs
+    order_keys = order_keys or _order_keys
     G = dist.get_world_size(group)
     srt = local_sort(local)
     if G == 1:
         return srt
-    spl = choose_splitters(srt, group, samples_per_rank, local_sort)
+    ordk = order_keys(srt)  # nondecreasing int64, the library's order
+    spl = choose_splitters(ordk, group, samples_per_rank, local_sort)
     if spl.numel() != G - 1:
         return srt  # no rank holds any key
-    # bucket q gets splitter[q-1] <= key < splitter[q]
-    cuts = torch.searchsorted(srt, spl, right=False) if spl.numel() else torch.zeros(0, dtype=torch.int64)
+    # bucket q gets splitter[q-1] <= key < splitter[q] (in the library's order)
+    cuts = torch.searchsorted(ordk, spl, right=False)
     edges = torch.cat([torch.zeros(1, dtype=torch.int64, device=srt.device), cuts.to(torch.int64),
                        torch.tensor([srt.numel()], dtype=torch.int64, device=srt.device)])
-    send = (edges[1:] - edges[:-1]).to(torch.int64)
+    send = _comm((edges[1:] - edges[:-1]).to(torch.int64), group)
     recv = torch.empty_like(send)
     dist.all_to_all_single(recv, send, group=group)
     send_l, recv_l = send.tolist(), recv.tolist()
-    out = torch.empty(int(sum(recv_l)), dtype=srt.dtype, device=srt.device)
-    dist.all_to_all_single(out, srt, output_split_sizes=recv_l, input_split_sizes=send_l, group=group)
+    # the keys travel as bits of the same-size signed type (gloo has no
+    # unsigned 64-bit collectives); only their bits matter here
+    wire = {torch.uint64: torch.int64, torch.uint32: torch.int32}.get(srt.dtype, srt.dtype)
+    payload = _comm(srt.view(wire), group)
+    out = torch.empty(int(sum(recv_l)), dtype=wire, device=payload.device)
+    dist.all_to_all_single(out, payload, output_split_sizes=recv_l, input_split_sizes=send_l, group=group)
+    out = out.to(srt.device).view(srt.dtype)
     offsets = np.concatenate([[0], np.cumsum(recv_l)]).astype(np.int64)
     if out.numel() == 0:
         return out

@@ -129,6 +129,26 @@ def uniform_int32_torch(n: int, seed: int = DEFAULT_SEED, device="cuda"):
     return out
 
 
+def int32_keys_torch(dist: str, n: int, seed: int = DEFAULT_SEED, device="cuda"):
+    """int32_keys(dist, n, seed), generated on `device` as a torch int32 tensor."""
+    import torch
+    if dist == "uniform":
+        return uniform_int32_torch(n, seed, device)
+    if dist in ("sorted", "reverse"):
+        i = torch.arange(n, dtype=torch.int64, device=device)
+        v = ((i << 32) // max(n, 1) - (1 << 31)).to(torch.int32)
+        return v if dist == "sorted" else v.flip(0).contiguous()
+    if dist == "dup16":
+        out = torch.empty(n, dtype=torch.int32, device=device)
+        chunk = 1 << 26
+        for c0 in range(0, n, chunk):
+            c1 = min(n, c0 + chunk)
+            k = splitmix64_torch(seed ^ STREAM_KEYS, c0, c1 - c0, device) & 15
+            out[c0:c1] = (k * (1 << 28) - (1 << 31)).to(torch.int32)
+        return out
+    raise ValueError(dist)
+
+
 def uniform_uint64_torch(n: int, seed: int = DEFAULT_SEED, device="cuda"):
     """uniform_uint64(n, seed), generated on `device` (bits in a torch int64 tensor)."""
     return splitmix64_torch(seed ^ STREAM_KEYS, 0, n, device)

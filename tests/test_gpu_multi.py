@@ -90,3 +90,78 @@ def test_unsorted_runs_and_overlapping_offsets_stay_in_bounds(sorter):
         sorter.sync()
         assert np.array_equal(out.cpu().numpy(), np.sort(x))
     abi.bs_set_option(sorter.h, "merge_kernel", "auto")
+
+
+def _gpu_exchange_worker(rank, world, port, sizes, kind, q):
+    """One rank of the exchange sort: keys on GPU 0 (shared by the ranks), the
+    library's sort, order keys and merge on the device, the collectives on
+    host copies (gloo)."""
+    import datetime
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from paper_1105_6040_gb300 import distributed as D
+    torch.cuda.set_device(0)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=90))
+    try:
+        x = _exchange_keys(rank, sizes[rank], kind)
+        dev = torch.from_numpy(x.view(np.int64)).cuda().view(torch.uint64) if kind == "uint64" \
+            else torch.from_numpy(x).cuda()
+        part = D.exchange_sort(dev)
+        torch.cuda.synchronize()
+        host = part.view(torch.int64).cpu().numpy().view(np.uint64) if kind == "uint64" else part.cpu().numpy()
+        gathered = [None] * world
+        dist.all_gather_object(gathered, host)
+        if rank == 0:
+            q.put(gathered)
+    finally:
+        dist.destroy_process_group()
+
+
+def _exchange_keys(rank, n, kind):
+    if kind == "int32":
+        return W.uniform_int32(n, seed=600 + rank)
+    if kind == "uint64":
+        return W.uniform_uint64(n, seed=600 + rank)
+    if kind == "float32_bits":
+        return W.uniform_float32_bits(n, seed=600 + rank)   # NaNs of both signs, -0, infinities
+    return W.normal_float32_edges(n, seed=600 + rank)      # +-inf, +-0 among normal values
+
+
+@pytest.mark.parametrize("sizes,kind", [
+    ([300001, 123457], "int32"), ([200000, 70001], "float32_bits"),
+    ([150000, 150000], "float32_edges"), ([100003, 90001], "uint64"),
+])
+def test_exchange_sort_two_ranks_share_one_gpu(sizes, kind):
+    """World size 2 through the library: two gloo processes on the one GPU,
+    local sort (bs_sort_keys), splitters and cuts in the library's order
+    (bs_order_keys), one all-to-all of host copies, merge of the received runs
+    (bs_merge_runs); the ranks' parts concatenated equal the oracle's sort of
+    both inputs, bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import socket
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_gpu_exchange_worker, args=(r, 2, port, sizes, kind, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        gathered = q.get(timeout=240)
+    finally:
+        for p in procs:
+            p.join(timeout=120)
+    for p in procs:
+        assert p.exitcode == 0
+    want, _ = oracle.sort(np.concatenate([_exchange_keys(r, sizes[r], kind) for r in range(2)]))
+    got = np.concatenate(gathered)
+    bits = np.uint32 if got.dtype.itemsize == 4 else np.uint64
+    assert np.array_equal(got.view(bits), want.view(bits))
+    assert all(g.size > 0 for g in gathered)  # the splitters cut the data between the ranks

@@ -30,3 +30,11 @@ def test_splitmix64_reference_values():
     assert [int(v) for v in got] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
     t = W.splitmix64_torch(0, 0, 3, device="cpu").numpy().view(np.uint64)
     assert np.array_equal(got, t)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "reverse", "dup16"])
+@pytest.mark.parametrize("n", [1, 1000, (1 << 20) + 7])
+def test_torch_int32_distributions_match_numpy(dist, n):
+    a = W.int32_keys(dist, n, seed=0xB5EED005)
+    b = W.int32_keys_torch(dist, n, seed=0xB5EED005, device="cpu").numpy()
+    assert np.array_equal(a, b)
