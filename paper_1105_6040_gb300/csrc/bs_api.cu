@@ -163,6 +163,108 @@ __global__ void tile_scan_add_kernel(int64_t *tprefix, const int64_t *bsum, int6
         tprefix[i + 1] += bsum[i / SCAN_BLOCK];
 }
 
+// The plan of a sort in one kernel, for up to PLAN_MAX_CHUNKS chunks of
+// SCAN_BLOCK blocks: the block bounds -- balanced ones b_i = floor(i*n/p)
+// written to off_w (Fig. 1, scatter phase), or the caller's offsets (and
+// gathered sources) checked, as validate_offsets_kernel and
+// validate_gather_kernel do --, each block's tile count and their exclusive
+// scan into tprefix, and `nzero` words (the persistent merge's counters)
+// zeroed.  CTA c < nsb scans chunk c on its own (tprefix[i+1] = the tiles of
+// the chunk's blocks up to i); every CTA zeroes a share of the words; the
+// last CTA to finish, found by a ticket it then resets to zero, turns the
+// chunk totals into offsets and adds them to the later chunks' entries.  No
+// CTA waits for another, so the kernel needs no co-resident grid.
+constexpr int PLAN_MAX_CHUNKS = 64;
+
+__global__ void __launch_bounds__(SCAN_TH)
+plan_scan_kernel(int64_t *off_w, const int64_t *off_r, int64_t S, int64_t n, int64_t p, int logT,
+                 int64_t max_len, const int64_t *src_off, int64_t n_in, int *err, int64_t *tprefix,
+                 int64_t *bsum, unsigned *ticket, unsigned *zero, int64_t nzero) {
+    __shared__ int64_t warp_tot[SCAN_TH / 32];
+    __shared__ int64_t chunk_base[PLAN_MAX_CHUNKS];
+    __shared__ int last;
+    griddep_wait();
+    const int64_t nsb = (S + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    for (int64_t i = blockIdx.x * (int64_t)SCAN_TH + threadIdx.x; i < nzero; i += (int64_t)gridDim.x * SCAN_TH)
+        zero[i] = 0u;
+    if (blockIdx.x < nsb) {
+        const int64_t base = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x * (int64_t)SCAN_IT;
+        int64_t v[SCAN_IT];
+        int64_t run = 0;
+#pragma unroll
+        for (int u = 0; u < SCAN_IT; ++u) {
+            const int64_t i = base + u;
+            int64_t t = 0;
+            if (i < S) {
+                int64_t lo, hi;
+                if (off_w) {
+                    lo = (int64_t)(((unsigned __int128)(uint64_t)i * (uint64_t)n) / (uint64_t)p);
+                    hi = (int64_t)(((unsigned __int128)(uint64_t)(i + 1) * (uint64_t)n) / (uint64_t)p);
+                    off_w[i] = lo;
+                    if (i == S - 1) off_w[S] = hi;
+                } else {
+                    lo = off_r[i];
+                    hi = off_r[i + 1];
+                    bool bad = hi < lo || lo < 0 || hi > n || (max_len > 0 && hi - lo > max_len);
+                    if (i == 0 && lo != 0) bad = true;
+                    if (i == S - 1 && hi != n) bad = true;
+                    if (src_off) {
+                        const int64_t so = src_off[i], len = hi - lo;
+                        if (so < 0 || len < 0 || so > n_in - len) bad = true;
+                    }
+                    if (bad) atomicCAS(err, 0, (int)BS_ERR_INVALID_ARG);
+                    lo = clamp64(lo, 0, n);
+                    hi = clamp64(hi, lo, n);
+                }
+                t = (hi - lo + (int64_t(1) << logT) - 1) >> logT;
+            }
+            run += t;
+            v[u] = run;
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int64_t x = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        int64_t wprefix = 0;
+        for (int w = 0; w < wid; ++w) wprefix += warp_tot[w];
+        const int64_t excl = wprefix + x - run;
+#pragma unroll
+        for (int u = 0; u < SCAN_IT; ++u) {
+            const int64_t i = base + u;
+            if (i < S) tprefix[i + 1] = excl + v[u];
+        }
+        if (threadIdx.x == SCAN_TH - 1) bsum[blockIdx.x] = excl + run;
+        if (blockIdx.x == 0 && threadIdx.x == 0) tprefix[0] = 0;
+    }
+    // the last CTA to finish adds the earlier chunks' totals
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's writes, before its ticket
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();  // every CTA's writes (their tickets came first)
+    if (nsb > 1) {
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int64_t c = 0; c < nsb; ++c) {
+                chunk_base[c] = acc;
+                acc += __ldcg(bsum + c);
+            }
+        }
+        __syncthreads();
+        for (int64_t i = SCAN_BLOCK + threadIdx.x; i < S; i += SCAN_TH)
+            tprefix[i + 1] = __ldcg(tprefix + i + 1) + chunk_base[i / SCAN_BLOCK];
+    }
+    if (threadIdx.x == 0) *ticket = 0u;  // ready for the next sort
+}
+
 // tseg[t] = the segment owning tile t (t < total tiles).
 __global__ void tile_map_kernel(const int64_t *tprefix, int64_t S, int32_t *tseg, int64_t ub) {
     griddep_wait();
@@ -188,6 +290,7 @@ struct bs_handle {
     size_t ws_bytes = 0;
     int *d_err = nullptr;
     unsigned long long *d_counters = nullptr;
+    unsigned *d_ticket = nullptr;  // plan_scan_kernel's ticket: zero between sorts
     int64_t launches[BS_KERNEL_CLASSES] = {0, 0, 0, 0};
     int logT = 12;
     int merge_impl = MERGE_AUTO;
@@ -417,12 +520,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     }
     const bool persist = h->persistent && !oddeven;
     const int64_t pwords = persist_words((int)Lmax0, ub0, g.R, blocks);
-    if (persist && pwords <= W.pcnt_words) {
-        launch_begin(h, CLS_SETUP, stream);
-        launch_overlapped(zero_words_kernel, blocks_for(pwords, 256, h->sms * 8), 256, 0, stream,
-                          (unsigned *)(ws + W.pcnt), pwords);
-        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
-    }
+    const int64_t nzero = (persist && pwords <= W.pcnt_words) ? pwords : 0;
     if (oddeven) {
         // scatter + encode into the padded buffer A; then sort A in place
         void *A = ws + W.total;
@@ -435,37 +533,59 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
         g.R = 0;
     }
     const int cap = h->sms * 8;
-    if (balanced) {
-        int64_t *off = (int64_t *)(ws + W.off);
-        launch_begin(h, CLS_SETUP, stream);
-        launch_overlapped(balanced_offsets_kernel, blocks_for(p + 1, 256, cap), 256, 0, stream, off, n, p);
-        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
-        g.off = off;
-    } else {
-        launch_begin(h, CLS_SETUP, stream);
-        launch_overlapped(validate_offsets_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off, S, n,
-                          max_len, h->d_err);
-        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    int64_t *tprefix = (int64_t *)(ws + W.tprefix);
+    int64_t *bsum = (int64_t *)(ws + W.bsum);
+    const int64_t nsb = (blocks + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (!balanced) {
         g.off = user_off;
         if (src_off) {
-            launch_begin(h, CLS_SETUP, stream);
-            launch_overlapped(validate_gather_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off,
-                              src_off, S, n_in, h->d_err);
-            if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
             g.src_off = src_off;
             g.n_in = n_in;
         }
     }
-
-    // tile map: exclusive scan of tiles per block, then tile -> block
-    int64_t *tprefix = (int64_t *)(ws + W.tprefix);
-    int64_t *bsum = (int64_t *)(ws + W.bsum);
-    const int64_t nsb = (blocks + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    launch_begin(h, CLS_SETUP, stream);
-    launch_overlapped(tile_scan_block_kernel, (unsigned)nsb, SCAN_TH, 0, stream, g.off, blocks, n, g.logT,
-                      tprefix, bsum);
-    if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
-    if (nsb > 1) {
+    if (nsb <= PLAN_MAX_CHUNKS) {
+        // bounds or their checks, tile scan and counter zeroing in one kernel
+        int64_t *off_w = balanced ? (int64_t *)(ws + W.off) : nullptr;
+        if (balanced) g.off = off_w;
+        int64_t zc = (nzero + SCAN_TH * 16 - 1) / (SCAN_TH * 16);
+        if (zc > 2 * (int64_t)h->sms) zc = 2 * (int64_t)h->sms;
+        const int64_t grid = nsb > zc ? nsb : zc;
+        launch_begin(h, CLS_SETUP, stream);
+        launch_overlapped(plan_scan_kernel, (unsigned)(grid > 0 ? grid : 1), SCAN_TH, 0, stream, off_w,
+                          balanced ? nullptr : user_off, blocks, n, balanced ? p : int64_t(1), g.logT,
+                          balanced ? int64_t(0) : max_len, balanced ? nullptr : src_off, n_in, h->d_err,
+                          tprefix, bsum, h->d_ticket, (unsigned *)(ws + W.pcnt), nzero);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    } else {
+        if (nzero) {
+            launch_begin(h, CLS_SETUP, stream);
+            launch_overlapped(zero_words_kernel, blocks_for(nzero, 256, h->sms * 8), 256, 0, stream,
+                              (unsigned *)(ws + W.pcnt), nzero);
+            if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+        }
+        if (balanced) {
+            int64_t *off = (int64_t *)(ws + W.off);
+            launch_begin(h, CLS_SETUP, stream);
+            launch_overlapped(balanced_offsets_kernel, blocks_for(p + 1, 256, cap), 256, 0, stream, off, n, p);
+            if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+            g.off = off;
+        } else {
+            launch_begin(h, CLS_SETUP, stream);
+            launch_overlapped(validate_offsets_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off, S, n,
+                              max_len, h->d_err);
+            if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+            if (src_off) {
+                launch_begin(h, CLS_SETUP, stream);
+                launch_overlapped(validate_gather_kernel, blocks_for(S, 256, cap), 256, 0, stream, user_off,
+                                  src_off, S, n_in, h->d_err);
+                if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+            }
+        }
+        // exclusive scan of tiles per block
+        launch_begin(h, CLS_SETUP, stream);
+        launch_overlapped(tile_scan_block_kernel, (unsigned)nsb, SCAN_TH, 0, stream, g.off, blocks, n, g.logT,
+                          tprefix, bsum);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
         launch_begin(h, CLS_SETUP, stream);
         launch_overlapped(tile_scan_top_kernel, 1, 1024, 0, stream, bsum, nsb);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
@@ -474,6 +594,8 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
                           blocks);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     }
+
+    // tile map: tile -> block
     const int64_t T = int64_t(1) << g.logT;
     const int64_t ub = (n + T - 1) / T + blocks;
     g.ntiles_ub = ub;
@@ -547,6 +669,7 @@ bs_status bs_create(bs_handle **out, int device) {
     if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) h->sms = 1;
     if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->d_counters, sizeof(unsigned long long) * BS_KERNEL_CLASSES) != cudaSuccess ||
+        cudaMalloc(&h->d_ticket, sizeof(unsigned)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         bs_destroy(h);
@@ -554,6 +677,7 @@ bs_status bs_create(bs_handle **out, int device) {
     }
     cudaMemset(h->d_err, 0, sizeof(int));
     cudaMemset(h->d_counters, 0, sizeof(unsigned long long) * BS_KERNEL_CLASSES);
+    cudaMemset(h->d_ticket, 0, sizeof(unsigned));
     if (cudaDeviceSynchronize() != cudaSuccess) {
         bs_destroy(h);
         return BS_ERR_CUDA;
@@ -575,6 +699,7 @@ bs_status bs_destroy(bs_handle *h) {
     if (h->hb) cudaFree(h->hb);
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_counters) cudaFree(h->d_counters);
+    if (h->d_ticket) cudaFree(h->d_ticket);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     for (int j = 0; j < 2; ++j) {
         if (h->ab[j]) cudaFree(h->ab[j]);
@@ -965,6 +1090,7 @@ bs_status bs_launch_stats(bs_handle *h, int64_t *counts, double *bytes, int rese
         for (int k = 0; k < BS_KERNEL_CLASSES; ++k) h->launches[k] = 0;
         cudaDeviceSynchronize();
         cudaMemset(h->d_counters, 0, sizeof(unsigned long long) * BS_KERNEL_CLASSES);
+    cudaMemset(h->d_ticket, 0, sizeof(unsigned));
         cudaDeviceSynchronize();
     }
     return BS_OK;

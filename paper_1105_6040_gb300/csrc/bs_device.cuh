@@ -1160,18 +1160,18 @@ __global__ void encode_copy_kernel(const K *__restrict__ in_k, const V *__restri
 
 // Odd-even schedule: scatter the n keys of p balanced blocks (bounds
 // floor(i*n/p)) into p slots of `cap` keys each, encoded; the slots past a
-// block's keys hold the largest code (+infinity sentinels).
+// block's keys hold the largest code (+infinity sentinels).  Grid: x chunks
+// of a slot by y slots, so every thread computes its slot's bounds once.
 template <class K>
 __global__ void pad_scatter_kernel(const K *__restrict__ in, K *out, int64_t n, int64_t p, int64_t cap,
                                    int codec) {
     griddep_wait();
-    const int64_t total = p * cap;
-    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < total;
-         y += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = y / cap, l = y - i * cap;
+    for (int64_t i = blockIdx.y; i < p; i += gridDim.y) {
         const int64_t b0 = (int64_t)(((unsigned __int128)(uint64_t)i * (uint64_t)n) / (uint64_t)p);
         const int64_t b1 = (int64_t)(((unsigned __int128)(uint64_t)(i + 1) * (uint64_t)n) / (uint64_t)p);
-        out[y] = l < b1 - b0 ? enc_code(in[b0 + l], codec) : max_code<K>();
+        K *o = out + i * cap;
+        for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < cap; l += (int64_t)gridDim.x * blockDim.x)
+            o[l] = l < b1 - b0 ? enc_code(in[b0 + l], codec) : max_code<K>();
     }
 }
 

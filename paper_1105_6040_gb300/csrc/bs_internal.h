@@ -14,10 +14,10 @@ namespace bs {
 // it on the stream drains, which hides most of the gap between two kernels.
 // Only kernels that wait before touching global memory are launched so.
 template <class... Params, class... Args>
-inline cudaError_t launch_overlapped(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
+inline cudaError_t launch_overlapped(void (*kern)(Params...), dim3 grid, unsigned block, size_t smem,
                                      cudaStream_t stream, Args... args) {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = grid;
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;

@@ -354,8 +354,14 @@ template <class K>
 bs_status oddeven_scatter_t(const void *in, void *out, int64_t n, int64_t p, int64_t cap, int codec,
                             Launcher &L) {
     L.begin(L.owner, CLS_SETUP, L.stream);
-    launch_overlapped(pad_scatter_kernel<K>, (unsigned)grid_for((p * cap + 255) / 256, (int64_t)L.sms * 8),
-                      256, 0, L.stream, (const K *)in, (K *)out, n, p, cap, codec);
+    // about 8 CTAs per SM in all: chunks of a slot by (at most 65535) slots
+    const int64_t ys = p < 65535 ? p : 65535;
+    int64_t xs = ((int64_t)L.sms * 8 + ys - 1) / ys;
+    const int64_t per_slot = (cap + 255) / 256;
+    if (xs > per_slot) xs = per_slot;
+    if (xs < 1) xs = 1;
+    launch_overlapped(pad_scatter_kernel<K>, dim3((unsigned)xs, (unsigned)ys), 256, 0, L.stream, (const K *)in,
+                      (K *)out, n, p, cap, codec);
     return L.end(L.owner, CLS_SETUP, L.stream) ? BS_OK : BS_ERR_CUDA;
 }
 
