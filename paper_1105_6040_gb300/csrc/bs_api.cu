@@ -169,7 +169,8 @@ __global__ void tile_scan_add_kernel(int64_t *tprefix, const int64_t *bsum, int6
 // gathered sources) checked, as validate_offsets_kernel and
 // validate_gather_kernel do --, each block's tile count and their exclusive
 // scan into tprefix, and `nzero` words (the persistent merge's counters)
-// zeroed.  CTA c < nsb scans chunk c on its own (tprefix[i+1] = the tiles of
+// zeroed.  Blocks of at most wmax keys get no tiles (the tile sort's warp
+// length class sorts them).  CTA c < nsb scans chunk c on its own (tprefix[i+1] = the tiles of
 // the chunk's blocks up to i); every CTA zeroes a share of the words; the
 // last CTA to finish, found by a ticket it then resets to zero, turns the
 // chunk totals into offsets and adds them to the later chunks' entries.  No
@@ -178,8 +179,8 @@ constexpr int PLAN_MAX_CHUNKS = 64;
 
 __global__ void __launch_bounds__(SCAN_TH)
 plan_scan_kernel(int64_t *off_w, const int64_t *off_r, int64_t S, int64_t n, int64_t p, int logT,
-                 int64_t max_len, const int64_t *src_off, int64_t n_in, int *err, int64_t *tprefix,
-                 int64_t *bsum, unsigned *ticket, unsigned *zero, int64_t nzero) {
+                 int64_t wmax, int64_t max_len, const int64_t *src_off, int64_t n_in, int *err,
+                 int64_t *tprefix, int64_t *bsum, unsigned *ticket, unsigned *zero, int64_t nzero) {
     __shared__ int64_t warp_tot[SCAN_TH / 32];
     __shared__ int64_t chunk_base[PLAN_MAX_CHUNKS];
     __shared__ int last;
@@ -216,7 +217,8 @@ plan_scan_kernel(int64_t *off_w, const int64_t *off_r, int64_t S, int64_t n, int
                     lo = clamp64(lo, 0, n);
                     hi = clamp64(hi, lo, n);
                 }
-                t = (hi - lo + (int64_t(1) << logT) - 1) >> logT;
+                // a segment of the warp length class has no tiles
+                t = hi - lo <= wmax ? 0 : (hi - lo + (int64_t(1) << logT) - 1) >> logT;
             }
             run += t;
             v[u] = run;
@@ -304,6 +306,7 @@ struct bs_handle {
     int host_direct = 1;      // bs_sort_keys_host: address page-locked host buffers directly
     int count_bytes = 0;      // kernels count algorithmic bytes (BS_OPT_COUNT_BYTES)
     int persistent = 1;       // every merge level in one persistent launch (BS_OPT_MERGE_PERSISTENT)
+    int length_classes = 1;   // warp length class for short segments (BS_OPT_LENGTH_CLASSES)
     cudaStream_t last_stream = nullptr;
     // per-launch timing
     bool timing = false;
@@ -543,6 +546,11 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
             g.n_in = n_in;
         }
     }
+    // the warp length class: keys alone, the default tile sort, tree schedule
+    // (balanced blocks: only when they are that short)
+    if (h->length_classes && vbytes == 0 && h->local_sort == BS_LOCAL_MERGE && !oddeven &&
+        nsb <= PLAN_MAX_CHUNKS && (!balanced || (n + p - 1) / p <= warp_class_max(g.logT)))
+        g.wmax = warp_class_max(g.logT);
     if (nsb <= PLAN_MAX_CHUNKS) {
         // bounds or their checks, tile scan and counter zeroing in one kernel
         int64_t *off_w = balanced ? (int64_t *)(ws + W.off) : nullptr;
@@ -553,7 +561,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
         launch_begin(h, CLS_SETUP, stream);
         launch_overlapped(plan_scan_kernel, (unsigned)(grid > 0 ? grid : 1), SCAN_TH, 0, stream, off_w,
                           balanced ? nullptr : user_off, blocks, n, balanced ? p : int64_t(1), g.logT,
-                          balanced ? int64_t(0) : max_len, balanced ? nullptr : src_off, n_in, h->d_err,
+                          g.wmax, balanced ? int64_t(0) : max_len, balanced ? nullptr : src_off, n_in, h->d_err,
                           tprefix, bsum, h->d_ticket, (unsigned *)(ws + W.pcnt), nzero);
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     } else {
@@ -595,14 +603,17 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     }
 
-    // tile map: tile -> block
+    // tile map: tile -> block (none when every block is in the warp length class)
     const int64_t T = int64_t(1) << g.logT;
     const int64_t ub = (n + T - 1) / T + blocks;
+    const bool no_tiles = balanced && g.wmax > 0;
     g.ntiles_ub = ub;
-    launch_begin(h, CLS_SETUP, stream);
-    launch_overlapped(tile_map_kernel, blocks_for(ub, 256, cap), 256, 0, stream, tprefix, blocks,
-                      (int32_t *)g.tseg, ub);
-    if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    if (!no_tiles) {
+        launch_begin(h, CLS_SETUP, stream);
+        launch_overlapped(tile_map_kernel, blocks_for(ub, 256, cap), 256, 0, stream, tprefix, blocks,
+                          (int32_t *)g.tseg, ub);
+        if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
+    }
 
     PassArgs a{};
     a.g = g;  // g.ntiles_ub is set above, before the tile map launch
@@ -634,6 +645,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.persistent = persist && pwords <= W.pcnt_words;
     a.pcnt = (unsigned *)(ws + W.pcnt);
     a.pcnt_words = pwords;
+    a.no_tiles = no_tiles;
     st = kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
     if (st != BS_OK || !oddeven) return st;
     // after p rounds the keys are in buffer (p & 1): decode the first n
@@ -1176,6 +1188,10 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
         h->persistent = (int)value;
         return BS_OK;
+    case BS_OPT_LENGTH_CLASSES:
+        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        h->length_classes = (int)value;
+        return BS_OK;
     default:
         return BS_ERR_INVALID_ARG;
     }
@@ -1224,6 +1240,7 @@ bs_status capture_graph(bs_handle *h, size_t ws_bytes, Body body, bs_graph **out
     g->h->merge_consumer = h->merge_consumer;
     g->h->count_bytes = h->count_bytes;
     g->h->persistent = h->persistent;
+    g->h->length_classes = h->length_classes;
     DevGuard dg(h->device);
     st = ensure_ws(g->h, ws_bytes);  // allocate before capture: nothing allocates inside it
     if (st == BS_OK && cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -102,6 +102,8 @@ struct Geo {
     int withhold;                  // test hook: CTA 0's producer withholds its first stage
     void *fin_k, *fin_v;           // final (decoded) outputs go here when set, else to
                                    // buffer 0 (e.g. pinned host memory the GPU addresses)
+    int64_t wmax;                  // length class: segments of 1..wmax keys have no tiles
+                                   // and one warp sorts each (0: every segment has tiles)
 };
 
 // Destination of a pass's output: the final buffers when this is the last
@@ -456,8 +458,14 @@ template <class K, class V> __host__ __device__ constexpr size_t tile_smem_bytes
 // special case: B's sentinel then ties with A's head and A is taken.  A lane
 // never consumes more than the 2m - diag keys left in its pair, so no read
 // passes B's sentinel, whatever the keys.
+//
+// Short tiles.  Keys at positions >= nreal (the tile's key count) are
+// padding: the largest code.  They stay at positions >= nreal after every
+// round (each run's real keys sort to its front), so a warp whose outputs
+// all lie there writes the largest code without merging, and in the last
+// round, whose positions >= nreal are never stored, nothing at all.
 template <class K, int THREADS, int KPT>
-__device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, int tid) {
+__device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, int tid, int nreal) {
     constexpr int T = THREADS * KPT;
     constexpr int M0 = 32 * KPT;  // run length after the warp rounds
     constexpr int WO = M0;        // outputs per warp per round
@@ -490,7 +498,10 @@ __device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, in
         if (!last && (p & 1) && (w * WO) % (2 * m) + WO == 2 * m && lane == 31)
             out[2 * m] = max_code<K>();  // the next round's B sentinel
         out += diag;
-        if (first) {
+        if (w * WO >= nreal) {
+            if (!last)
+                for (int u = 0; u < cnt; ++u) out[u] = max_code<K>();
+        } else if (first) {
             const K *pb0 = src + p * R1;
             auto at = [&](int e) { return pb0[e + (e >> 5)]; };
             int lo = diag > m ? diag - m : 0, hi = diag < m ? diag : m;
@@ -564,6 +575,87 @@ __device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, in
     return src;
 }
 
+// The warp length class of the sort phase: every segment of 1..g.wmax keys
+// (wmax <= 32*KPT; the plan gave these segments no tiles) is sorted whole by
+// one warp -- KPT keys per lane through the register network, then the five
+// shuffle rounds leave lane l holding outputs l*KPT .. l*KPT+KPT-1 -- and
+// stored through the warp's own shared-memory buffer `wb` (33*KPT keys,
+// padded so that neither the blocked write nor the striped read conflicts)
+// as coalesced rows.  Warp gw of nw takes segments gw, gw+nw, gw+2nw, ..;
+// its lanes read 32 candidates' bounds at a time and the warp sorts the ones
+// in the class one after another.  A segment of this class is never merged
+// afterwards, so its result is final (or, with cross-block rounds, the
+// buffer the first round reads).  Returns the bytes it moved.  It runs as a
+// launch of its own: inside the tile sort kernel it changed that kernel's
+// register allocation.
+template <class K, int KPT>
+__device__ __forceinline__ unsigned long long warp_class_sort(const Geo &g, const K *__restrict__ in_k,
+                                                              K *buf_k0, K *buf_k1, int codec, K *wb,
+                                                              int lane, int64_t gw, int64_t nw) {
+    unsigned long long bytes = 0;
+    const bool fin = g.R == 0;
+    K *dst = out_buf<K>(fin, g.fin_k, g.R & 1, buf_k0, buf_k1);
+    for (int64_t i0 = 0; gw + nw * i0 < g.S; i0 += 32) {
+        const int64_t s = gw + nw * (i0 + lane);
+        int64_t lo = 0, hi = 0;
+        if (s < g.S) seg_bounds(g, s, lo, hi);
+        unsigned m = __ballot_sync(0xffffffffu, hi > lo && hi - lo <= g.wmax);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t ss = __shfl_sync(0xffffffffu, s, src);
+            const int64_t slo = __shfl_sync(0xffffffffu, lo, src);
+            const int len = (int)(__shfl_sync(0xffffffffu, hi, src) - slo);
+            int64_t ibase = slo;
+            int lcnt = len;
+            if (g.src_off) {
+                if (len <= g.n_in) ibase = clamp64(g.src_off[ss], 0, g.n_in - len);
+                else lcnt = 0;  // malformed request (flagged by the offset check): load nothing
+            }
+            K k[KPT];
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int pos = lane + 32 * u;
+                k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
+            }
+            reg_sort_keys<KPT>(k);
+#pragma unroll 1
+            for (int r = 0; r < 5; ++r) warp_merge_round<KPT>(k, r, lane);
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int e = lane * KPT + u;
+                wb[e + (e >> 5)] = k[u];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int pos = lane + 32 * u;
+                if (pos < len) {
+                    const K c = wb[pos + (pos >> 5)];
+                    dst[slo + pos] = fin ? dec_code(c, codec) : c;
+                }
+            }
+            __syncwarp();  // the buffer is free for the next segment
+            bytes += 2ull * sizeof(K) * (unsigned)len;
+        }
+    }
+    return bytes;
+}
+
+// The warp length class as its own launch (before the tile sort, which
+// never sees these segments): WARPS warps per CTA, each with its buffer.
+template <class K, int KPT, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
+warp_class_kernel(Geo g, const K *__restrict__ in_k, K *buf_k0, K *buf_k1, int codec) {
+    __shared__ K wb[WARPS][33 * KPT];
+    griddep_wait();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long b =
+        warp_class_sort<K, KPT>(g, in_k, buf_k0, buf_k1, codec, wb[w], lane,
+                                (int64_t)blockIdx.x * WARPS + w, (int64_t)gridDim.x * WARPS);
+    if (lane == 0 && b) count_bytes(g, CLS_TILE_SORT, b);
+}
+
 // Tile sort (the sort phase of Fig. 1 at CTA scale).  Tile t covers
 // keys [s + j*T, min(s + (j+1)*T, e)) of segment [s, e).  Each thread sorts
 // KPT keys in registers; keys-only tiles then merge pairs of lists with five
@@ -575,8 +667,16 @@ __device__ __forceinline__ const K *tile_smem_rounds(K (&k)[KPT], K *x, K *y, in
 // (code, original position), which is the stable order; values move once,
 // at the final store.  The sorted tile is written -- decoded if this is the
 // segment's last pass -- to the buffer its merge schedule starts from.
+// Resident CTAs per SM the keys-alone tile sort of 32-bit keys is compiled
+// for: as many as its shared memory allows (3 at 8192-key tiles, 6 at 4096;
+// 8 at 2048), so that the register allocation does not lower them.
+template <class K, class V, int THREADS, int KPT> constexpr int tile_min_ctas() {
+    return (sizeof(K) == 4 && !HasVal<V>::value) ? (THREADS * KPT == 8192 ? 3 : THREADS * KPT == 4096 ? 6 : 8)
+                                                 : 1;
+}
+
 template <class K, class V, int THREADS, int KPT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (tile_min_ctas<K, V, THREADS, KPT>()))
 tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
                  K *buf_k0, K *buf_k1, V *buf_v0, V *buf_v1, int codec,
                  const int64_t *__restrict__ ntiles_total) {
@@ -637,21 +737,26 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
             __syncthreads();  // the first round overwrites sk
             reg_sort_pairs<KPT>(k, x);
         } else {
+            // warp w loads positions [w*32*KPT, (w+1)*32*KPT), 32 consecutive
+            // keys per step; a warp past the last key holds padding alone,
+            // already in order, and skips the network and the shuffle rounds
+            const int lane = tid & 31, w0 = (tid >> 5) * 32 * KPT;
 #pragma unroll
             for (int u = 0; u < KPT; ++u) {
-                const int pos = tid + u * THREADS;
+                const int pos = w0 + lane + 32 * u;
                 k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
             }
-            reg_sort_keys<KPT>(k);
+            if (w0 < cnt) {
+                reg_sort_keys<KPT>(k);
+                // the first merges inside a warp: register shuffles, no shared memory
+#pragma unroll 1
+                for (int r = 0; r < 5; ++r) warp_merge_round<KPT>(k, r, lane);
+            }
         }
 
         if constexpr (!HV) {
-            // the first merges inside a warp: register shuffles, no shared memory
-            const int lane = tid & 31;
-#pragma unroll 1
-            for (int r = 0; r < 5; ++r) warp_merge_round<KPT>(k, r, lane);
             // then the shared-memory rounds, and the coalesced striped store
-            const K *res = tile_smem_rounds<K, THREADS, KPT>(k, sk, sk + keys_round_buf(T), tid);
+            const K *res = tile_smem_rounds<K, THREADS, KPT>(k, sk, sk + keys_round_buf(T), tid, cnt);
 #pragma unroll
             for (int u = 0; u < KPT; ++u) {
                 const int pos = tid + u * THREADS;

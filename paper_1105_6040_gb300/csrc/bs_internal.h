@@ -62,7 +62,13 @@ struct PassArgs {
     int persistent;           // 1: every merge level in one persistent launch where it can run
     unsigned *pcnt;           // its pair counters and work queue (zeroed before the sort phase)
     int64_t pcnt_words;       // capacity of pcnt in 32-bit words
+    bool no_tiles;            // every block is in the warp length class: no tile sort launch
 };
+
+// Longest segment of the warp length class for a keys-alone sort at tile
+// 2^logT: 32 lanes x the tile sort's keys per thread (32, or 16 at 2048-key
+// tiles).  Pair sorts and the alternative local sorts have no such class.
+inline int64_t warp_class_max(int logT) { return logT >= 12 ? 32 * 32 : 32 * 16; }
 
 // Words of the persistent merge's counter region for a sort whose in-block
 // levels number `nseg` over `ntiles_ub` sort tiles in S blocks and whose

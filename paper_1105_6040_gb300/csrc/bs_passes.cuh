@@ -302,12 +302,25 @@ bs_status run_passes_t(const PassArgs &a, Launcher &L) {
                           g, (const K *)a.in_k, k0, k1, a.codec, a.ntiles_total);
         if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
     } else {
+        if constexpr (!HasVal<V>::value) {
+            // sort phase, warp length class: the short segments, one warp each
+            if (g.wmax > 0) {
+                constexpr int WW = 4;
+                const int64_t warps = g.S < (int64_t)L.sms * 32 ? g.S : (int64_t)L.sms * 32;
+                L.begin(L.owner, CLS_TILE_SORT, L.stream);
+                launch_overlapped(warp_class_kernel<K, KPT, WW>, (unsigned)grid_for((warps + WW - 1) / WW, warps),
+                                  32 * WW, 0, L.stream, g, (const K *)a.in_k, k0, k1, a.codec);
+                if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+            }
+        }
         // sort phase: every tile of every block
-        L.begin(L.owner, CLS_TILE_SORT, L.stream);
-        launch_overlapped(ts, (unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem,
-                          L.stream, g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec,
-                          a.ntiles_total);
-        if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+        if (!a.no_tiles) {
+            L.begin(L.owner, CLS_TILE_SORT, L.stream);
+            launch_overlapped(ts, (unsigned)grid_for(a.ntiles_ub, (int64_t)L.sms * occ_ts), THREADS, tsmem,
+                              L.stream, g, (const K *)a.in_k, (const V *)a.in_v, k0, k1, v0, v1, a.codec,
+                              a.ntiles_total);
+            if (!L.end(L.owner, CLS_TILE_SORT, L.stream)) return BS_ERR_CUDA;
+        }
     }
 
     // every merge level in one persistent launch, where it can run
