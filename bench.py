@@ -210,7 +210,9 @@ def config(args):
             "merge_tile_keys": 1 << (args.merge_tile_log2 or args.tile_log2),
             "merge_consumer": ["thread sequential merge", "warp bitonic"][args.merge_consumer],
             "seed": SEED, "l2": "inputs (4 B x n = 1 GiB at 2^28) larger than the 129 MB L2; no flush",
-            "stream": "torch current stream", "out_of_place": True}
+            "stream": "torch current stream", "out_of_place": True,
+            "check": "warm-up output checked by the library's device checkers (bs_check_keys): "
+                     "nondecreasing, both multiset hashes equal to the input's"}
 
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
@@ -378,8 +380,12 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     sorter.sync()
-    # correctness of the warm-up output (cheap property checks on the device)
-    assert bool((d_out[1:] >= d_out[:-1]).all()), "output not sorted"
+    # correctness of the warm-up output: the library's device checkers (one
+    # pass each, outside the timed regions) -- sorted, same multiset of codes
+    chk_in, chk_out = abi.check_keys(d_in), abi.check_keys(d_out)
+    assert chk_out["first_unsorted"] == -1, "output not sorted"
+    assert (chk_out["hash_a"], chk_out["hash_b"]) == (chk_in["hash_a"], chk_in["hash_b"]), \
+        "output not a permutation of the input"
 
     # ---- timed region A: K whole sorts, CUDA events on the launching stream
     abi.bs_launch_stats(sorter.h, reset=True, with_bytes=False)

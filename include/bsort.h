@@ -206,6 +206,42 @@ bs_status bs_workspace_bytes(int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, siz
 bs_status bs_order_keys(const void *d_in, int64_t *d_out, int64_t n, bs_dtype kt, void *stream);
 
 /*
+ * Device checkers of a sort's result (test infrastructure; no counterpart
+ * in the paper, whose correctness criterion -- a nondecreasing permutation
+ * of the input, Sec. 3 -- they test in one pass over device memory).
+ * code(k) is the key's order-preserving code as a uint64 (4-byte codes
+ * zero-extended), the code the sort compares.
+ *   first_unsorted: the smallest i, 0 < i < n, with code(k[i-1]) > code(k[i])
+ *     where i does not start a segment (d_offsets: S+1 device offsets,
+ *     0 = off[0] <= .. <= off[S] = n; NULL: one run), else -1.
+ *   first_unstable: with d_idx (device, n payload indices of dtype it:
+ *     INT32, UINT32, INT64 or UINT64), the smallest such i with equal codes
+ *     and idx[i-1] >= idx[i], else -1 (always -1 without d_idx).
+ *   hash_a, hash_b: sum over all keys of mix_a(code) and mix_b(code) mod
+ *     2^64, multiset hashes equal for any permutation of the same keys.
+ *     mix_a(x): x ^= x >> 33; x *= 0xff51afd7ed558ccd; x ^= x >> 33;
+ *       x *= 0xc4ceb9fe1a85ec53; x ^= x >> 33 (MurmurHash3 fmix64).
+ *     mix_b(x): x += 0x632be59bd9b4e019; x ^= x >> 29; x *= 0xbf58476d1ce4e5b9;
+ *       x ^= x >> 32; x *= 0x94d049bb133111eb; x ^= x >> 29.
+ */
+typedef struct {
+    int64_t first_unsorted;
+    int64_t first_unstable;
+    uint64_t hash_a, hash_b;
+} bs_check_result;
+
+/*
+ * Runs the checkers on `stream` (the current device) and waits for them;
+ * *result (host memory) receives the outcome.  n = 0 gives -1, -1, 0, 0.
+ * It allocates a 32-byte accumulator from the stream-ordered allocator.
+ * Errors: INVALID_ARG (result NULL, n < 0, d_keys NULL with n > 0,
+ * d_offsets with S < 1), UNSUPPORTED_DTYPE (kt; it when d_idx is given),
+ * OUT_OF_MEMORY, CUDA.
+ */
+bs_status bs_check_keys(const void *d_keys, int64_t n, bs_dtype kt, const int64_t *d_offsets, int64_t S,
+                        const void *d_idx, bs_dtype it, bs_check_result *result, void *stream);
+
+/*
  * Grow the handle's scratch now to what one sort of n keys (value type vt,
  * BS_NONE for none) in S blocks or segments needs (bs_workspace_bytes), so
  * that later calls of up to that size and block/segment count allocate

@@ -43,6 +43,7 @@ SIGNATURES = {
     "bs_workspace_bytes": ([_I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
     "bs_reserve_workspace": ([_P, _I64, _I64, _INT, _INT, C.POINTER(C.c_size_t)], _INT),
     "bs_order_keys": ([_P, _P, _I64, _INT, _P], _INT),
+    "bs_check_keys": ([_P, _I64, _INT, _P, _I64, _P, _INT, _P, _P], _INT),
     "bs_sync_status": ([_P], _INT),
     "bs_status_str": ([_INT], C.c_char_p),
     "bs_launch_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double), _INT], _INT),
@@ -193,6 +194,38 @@ def order_keys(keys, stream=None):
     bs_order_keys(keys.data_ptr(), out.data_ptr(), keys.numel(), keys.dtype,
                   _stream_ptr(stream, keys.device))
     return out
+
+
+class CheckResult(C.Structure):
+    """bs_check_result: first offending positions (-1 = none) and the two
+    multiset hashes of the keys' codes."""
+    _fields_ = [("first_unsorted", C.c_int64), ("first_unstable", C.c_int64),
+                ("hash_a", C.c_uint64), ("hash_b", C.c_uint64)]
+
+
+def bs_check_keys(d_keys, n, kt, d_offsets=None, S=0, d_idx=None, it="none", stream=0) -> dict:
+    """The device checkers (one pass): first_unsorted / first_unstable
+    (-1 = none; segment starts excused when offsets are given) and hash_a /
+    hash_b of the keys' codes.  Waits for the result."""
+    r = CheckResult()
+    _check(load().bs_check_keys(d_keys, int(n), dtype_code(kt), d_offsets, int(S), d_idx,
+                                dtype_code(it) if d_idx else -1, C.byref(r), stream or None),
+           "bs_check_keys")
+    return {"first_unsorted": r.first_unsorted, "first_unstable": r.first_unstable,
+            "hash_a": r.hash_a, "hash_b": r.hash_b}
+
+
+def check_keys(keys, offsets=None, idx=None, stream=None) -> dict:
+    """bs_check_keys on CUDA tensors (keys of a key dtype; offsets int64,
+    S+1 entries; idx an integer tensor of payload positions)."""
+    for t, name in ((keys, "keys"), (offsets, "offsets"), (idx, "idx")):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return bs_check_keys(keys.data_ptr(), keys.numel(), keys.dtype,
+                         None if offsets is None else offsets.data_ptr(),
+                         0 if offsets is None else offsets.numel() - 1,
+                         None if idx is None else idx.data_ptr(),
+                         "none" if idx is None else idx.dtype, _stream_ptr(stream, keys.device))
 
 
 def bs_sync_status(h) -> int:

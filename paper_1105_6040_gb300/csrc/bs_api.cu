@@ -58,6 +58,103 @@ __global__ void order_keys_kernel(const K *__restrict__ in, int64_t *out, int64_
     }
 }
 
+// ---------------------------------------------------------------- device checkers
+
+// The two 64-bit mixes of the multiset hashes: MurmurHash3's fmix64
+// finaliser, and an add-xorshift-multiply mix (shifts 29, 32, 29), as
+// bsort.h defines them.
+__device__ __forceinline__ uint64_t check_mix_a(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+__device__ __forceinline__ uint64_t check_mix_b(uint64_t x) {
+    x += 0x632be59bd9b4e019ull;
+    x ^= x >> 29;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 32;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 29;
+    return x;
+}
+
+// Device-side accumulators of bs_check_keys: the smallest offending
+// positions (all ones = none) and the two hash sums.
+struct CheckAcc {
+    unsigned long long first_unsorted, first_unstable, hash_a, hash_b;
+};
+
+// Whether position i (0 < i < n) starts a segment: some off[s] == i.  A
+// binary search for the largest s with off[s] <= i (off[0] = 0 <= i and
+// off[S] = n > i bracket it); it runs only where the keys drop or tie.
+__device__ __forceinline__ bool check_seg_start(const int64_t *off, int64_t S, int64_t i) {
+    int64_t lo = 0, hi = S;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return off[lo] == i;
+}
+
+// One pass over the keys: each key's code into both hash sums; at every
+// position whose key is below its predecessor's (a drop), or equal to it
+// with a payload index not above the predecessor's (stability), the
+// position unless it starts a segment.  Index payloads are compared as
+// signed (isigned) or unsigned 64-bit integers.  One atomic per warp.
+template <class K>
+__global__ void check_keys_kernel(const K *__restrict__ keys, int64_t n, int codec, const int64_t *off,
+                                  int64_t S, const void *idx, int iw, int isigned, CheckAcc *acc) {
+    griddep_wait();
+    uint64_t ha = 0, hb = 0;
+    unsigned long long bad = ~0ull, unst = ~0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = (uint64_t)enc_code(keys[i], codec);
+        ha += check_mix_a(c);
+        hb += check_mix_b(c);
+        if (i == 0) continue;
+        const uint64_t pc = (uint64_t)enc_code(keys[i - 1], codec);
+        if (pc > c) {
+            if (!(off && check_seg_start(off, S, i)) && (unsigned long long)i < bad) bad = (unsigned long long)i;
+        } else if (pc == c && idx) {
+            uint64_t a, b;
+            if (iw == 4) {
+                const uint32_t *x = static_cast<const uint32_t *>(idx);
+                a = isigned ? (uint64_t)(int64_t)(int32_t)x[i - 1] : (uint64_t)x[i - 1];
+                b = isigned ? (uint64_t)(int64_t)(int32_t)x[i] : (uint64_t)x[i];
+            } else {
+                const uint64_t *x = static_cast<const uint64_t *>(idx);
+                a = x[i - 1];
+                b = x[i];
+            }
+            if (isigned) {  // signed order as unsigned: flip the sign bits
+                a ^= 0x8000000000000000ull;
+                b ^= 0x8000000000000000ull;
+            }
+            if (a >= b && !(off && check_seg_start(off, S, i)) && (unsigned long long)i < unst)
+                unst = (unsigned long long)i;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ha += __shfl_xor_sync(0xffffffffu, ha, d);
+        hb += __shfl_xor_sync(0xffffffffu, hb, d);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bad, d);
+        const unsigned long long ou = __shfl_xor_sync(0xffffffffu, unst, d);
+        bad = ob < bad ? ob : bad;
+        unst = ou < unst ? ou : unst;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc->hash_a, (unsigned long long)ha);
+        atomicAdd(&acc->hash_b, (unsigned long long)hb);
+        if (bad != ~0ull) atomicMin(&acc->first_unsorted, bad);
+        if (unst != ~0ull) atomicMin(&acc->first_unstable, unst);
+    }
+}
+
 // Caller offsets must start at 0, end at n, never decrease, and (when a
 // bound is given) hold no segment longer than max_len.
 __global__ void validate_offsets_kernel(const int64_t *off, int64_t S, int64_t n, int64_t max_len,
@@ -1040,6 +1137,64 @@ bs_status bs_order_keys(const void *d_in, int64_t *d_out, int64_t n, bs_dtype kt
     else
         launch_overlapped(order_keys_kernel<uint64_t>, grid, 256, 0, s, (const uint64_t *)d_in, d_out, n, key_codec(kt));
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+bs_status bs_check_keys(const void *d_keys, int64_t n, bs_dtype kt, const int64_t *d_offsets, int64_t S,
+                        const void *d_idx, bs_dtype it, bs_check_result *result, void *stream) {
+    if (!result || n < 0 || (d_offsets && S < 1)) return BS_ERR_INVALID_ARG;
+    const int kw = key_width(kt);
+    if (!kw) return BS_ERR_UNSUPPORTED_DTYPE;
+    int iw = 0, isigned = 0;
+    if (d_idx) {
+        switch (it) {
+        case BS_INT32: iw = 4, isigned = 1; break;
+        case BS_UINT32: iw = 4; break;
+        case BS_INT64: iw = 8, isigned = 1; break;
+        case BS_UINT64: iw = 8; break;
+        default: return BS_ERR_UNSUPPORTED_DTYPE;
+        }
+    }
+    if (n > 0 && !d_keys) return BS_ERR_INVALID_ARG;
+    result->first_unsorted = -1;
+    result->first_unstable = -1;
+    result->hash_a = result->hash_b = 0;
+    if (n == 0) return BS_OK;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    CheckAcc *acc = nullptr;
+    if (cudaMallocAsync((void **)&acc, sizeof(CheckAcc), s) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_OUT_OF_MEMORY;
+    }
+    CheckAcc host{};
+    bool ok = cudaMemsetAsync(acc, 0xff, 2 * sizeof(unsigned long long), s) == cudaSuccess &&
+              cudaMemsetAsync(&acc->hash_a, 0, 2 * sizeof(unsigned long long), s) == cudaSuccess;
+    if (ok) {
+        const unsigned grid = blocks_for(n, 256, sms * 8);
+        const int codec = key_codec(kt);
+        if (kw == 4)
+            launch_overlapped(check_keys_kernel<uint32_t>, grid, 256, 0, s, (const uint32_t *)d_keys, n, codec,
+                              d_offsets, S, d_idx, iw, isigned, acc);
+        else
+            launch_overlapped(check_keys_kernel<uint64_t>, grid, 256, 0, s, (const uint64_t *)d_keys, n, codec,
+                              d_offsets, S, d_idx, iw, isigned, acc);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemcpyAsync(&host, acc, sizeof(CheckAcc), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    }
+    cudaFreeAsync(acc, s);
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    result->first_unsorted = host.first_unsorted == ~0ull ? -1 : (int64_t)host.first_unsorted;
+    result->first_unstable = host.first_unstable == ~0ull ? -1 : (int64_t)host.first_unstable;
+    result->hash_a = host.hash_a;
+    result->hash_b = host.hash_b;
+    return BS_OK;
 }
 
 bs_status bs_reserve_workspace(bs_handle *h, int64_t n, int64_t S, bs_dtype kt, bs_dtype vt, size_t *bytes) {
