@@ -171,16 +171,17 @@ bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t
                             bs_dtype kt, int64_t p);
 
 /*
- * Asynchronous host-memory sort: enqueues the copy of h_in into one of the
- * handle's two device buffers (on an internal copy stream), the sort (as
- * bs_sort_keys: p blocks, Fig. 1; on `stream`) and the copy of the result into
- * h_out (may equal h_in; on a second internal copy stream), and returns.
- * Successive calls on one handle form a pipeline: call k+1's copy in and
- * call k-1's copy out run on the copy engines while call k sorts, and the
- * sorts of a handle run one after another whatever streams they are given.
+ * Asynchronous host-memory sort: enqueues the copy of h_in into the input
+ * buffer of one of the handle's two device slots (on an internal copy
+ * stream), the sort (as bs_sort_keys: p blocks, Fig. 1; on `stream`) into
+ * the slot's output buffer and the copy of the result into h_out (may equal
+ * h_in; on a second internal copy stream), and returns.  Successive calls on
+ * one handle form a pipeline: call k+1's copy in and call k-1's copy out run
+ * on the copy engines while call k sorts, neither waiting for the other, and
+ * the sorts of a handle run one after another whatever streams they are given.
  * h_in must stay unchanged and h_out unread until bs_sync_status(h), which
  * waits for all of the handle's work, returns.  The copies are asynchronous
- * only for page-locked buffers.  Device memory: two buffers of n keys
+ * only for page-locked buffers.  Device memory: four buffers of n keys
  * besides the workspace.  Errors as bs_sort_keys.
  */
 bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, int64_t n,

@@ -417,11 +417,11 @@ struct bs_handle {
     cudaStream_t own_stream = nullptr;
     void *hb = nullptr;
     size_t hb_bytes = 0;
-    // bs_sort_keys_host_async: two device buffers used in turn, a stream for
-    // the copies in and one for the copies out, and per buffer the events
-    // "copied in", "sorted", "copied out"
-    void *ab[2] = {nullptr, nullptr};
-    size_t ab_bytes[2] = {0, 0};
+    // bs_sort_keys_host_async: two slots used in turn, each an input and an
+    // output device buffer; a stream for the copies in and one for the
+    // copies out, and per slot the events "copied in", "sorted", "copied out"
+    void *ab[2] = {nullptr, nullptr}, *ob[2] = {nullptr, nullptr};
+    size_t ab_bytes[2] = {0, 0}, ob_bytes[2] = {0, 0};
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_sorted[2] = {nullptr, nullptr},
                 ev_out[2] = {nullptr, nullptr};
@@ -812,6 +812,7 @@ bs_status bs_destroy(bs_handle *h) {
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     for (int j = 0; j < 2; ++j) {
         if (h->ab[j]) cudaFree(h->ab[j]);
+        if (h->ob[j]) cudaFree(h->ob[j]);
         if (h->ev_in[j]) cudaEventDestroy(h->ev_in[j]);
         if (h->ev_sorted[j]) cudaEventDestroy(h->ev_sorted[j]);
         if (h->ev_out[j]) cudaEventDestroy(h->ev_out[j]);
@@ -1026,15 +1027,21 @@ static bs_status ensure_buf(void *&buf, size_t &have, size_t bytes) {
     return BS_OK;
 }
 
-// Call k of bs_sort_keys_host_async uses device buffer j = k % 2:
-//   copy-in stream:  wait "copied out"[j] (call k-2 is done with buffer j),
-//                    copy h_in -> buffer j, record "copied in"[j];
-//   caller's stream: wait "copied in"[j] and "sorted"[1-j] (call k-1's sort:
-//                    the workspace is shared), sort in place, record "sorted"[j];
-//   copy-out stream: wait "sorted"[j], copy buffer j -> h_out, record
+// Call k of bs_sort_keys_host_async uses slot j = k % 2 (input buffer in_j,
+// output buffer out_j):
+//   copy-in stream:  wait "sorted"[j] (call k-2 has read in_j), copy h_in ->
+//                    in_j, record "copied in"[j];
+//   caller's stream: wait "copied in"[j], "copied out"[j] (call k-2's copy
+//                    out has read out_j) and "sorted"[1-j] (call k-1's sort:
+//                    the workspace is shared), sort in_j -> out_j, record
+//                    "sorted"[j];
+//   copy-out stream: wait "sorted"[j], copy out_j -> h_out, record
 //                    "copied out"[j].
 // So call k+1's copy in and call k-1's copy out run on the copy engines while
-// call k sorts.  An event not yet recorded counts as complete.
+// call k sorts, and neither copy waits for the other: the copy in of call
+// k+2 needs only call k's sort, not its copy out (one buffer per slot made
+// the two copies chain behind each sort).  An event not yet recorded counts
+// as complete.
 bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
                                   int64_t p, void *stream) {
     if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
@@ -1056,19 +1063,21 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
     const int j = (int)(h->async_calls & 1);
     const size_t bytes = (size_t)n * kw;
     bs_status st = ensure_buf(h->ab[j], h->ab_bytes[j], bytes);
+    if (st == BS_OK) st = ensure_buf(h->ob[j], h->ob_bytes[j], bytes);
     if (st != BS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaStreamWaitEvent(h->cp_in, h->ev_out[j], 0) != cudaSuccess ||
+    if (cudaStreamWaitEvent(h->cp_in, h->ev_sorted[j], 0) != cudaSuccess ||
         cudaMemcpyAsync(h->ab[j], h_in, bytes, cudaMemcpyHostToDevice, h->cp_in) != cudaSuccess ||
         cudaEventRecord(h->ev_in[j], h->cp_in) != cudaSuccess ||
         cudaStreamWaitEvent(s, h->ev_in[j], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h->ev_out[j], 0) != cudaSuccess ||
         cudaStreamWaitEvent(s, h->ev_sorted[1 - j], 0) != cudaSuccess)
         return BS_ERR_CUDA;
-    st = bs_sort_keys(h, h->ab[j], h->ab[j], n, kt, p, (void *)s);
+    st = bs_sort_keys(h, h->ab[j], h->ob[j], n, kt, p, (void *)s);
     if (st != BS_OK) return st;
     if (cudaEventRecord(h->ev_sorted[j], s) != cudaSuccess ||
         cudaStreamWaitEvent(h->cp_out, h->ev_sorted[j], 0) != cudaSuccess ||
-        cudaMemcpyAsync(h_out, h->ab[j], bytes, cudaMemcpyDeviceToHost, h->cp_out) != cudaSuccess ||
+        cudaMemcpyAsync(h_out, h->ob[j], bytes, cudaMemcpyDeviceToHost, h->cp_out) != cudaSuccess ||
         cudaEventRecord(h->ev_out[j], h->cp_out) != cudaSuccess)
         return BS_ERR_CUDA;
     h->async_calls++;

@@ -317,7 +317,8 @@ def test_host_entry_direct_and_copy(direct, case):
 
 def test_host_async_pipeline():
     """bs_sort_keys_host_async: six calls in flight on one handle (its two
-    device buffers used in turn, copies overlapping sorts), interleaved with
+    slots of input and output buffers used in turn, copies overlapping
+    sorts), interleaved with
     calls on a second handle and stream; int32, float32 and uint64 keys,
     growing sizes (a buffer regrown between calls), one call in place and
     one from pageable memory.  Every result is the oracle's."""
