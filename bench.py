@@ -53,7 +53,7 @@ def parse_args():
                          "arrays of log-uniform length in one graph-captured segmented sort")
     ap.add_argument("--pairs-log2n", type=int, default=27)
     ap.add_argument("--pairs-dist", default="uniform", choices=["uniform", "zipf"])
-    ap.add_argument("--pairs-tile-log2", type=int, default=12)
+    ap.add_argument("--pairs-tile-log2", type=int, default=13)
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--seg-lo", type=int, default=16)
     ap.add_argument("--seg-hi-log2", type=int, default=17)
