@@ -185,3 +185,35 @@ def test_graph_replay_with_classes(sorters):
             assert np.array_equal(d_out.cpu().numpy(), want)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("direct", [1, 0])
+def test_host_entry_points_with_short_blocks(sorters, direct):
+    """bs_sort_keys_host with blocks in the class: with page-locked buffers
+    the class's warps read and write host memory directly (the tile sort's
+    role there), with pageable ones the keys are copied in and out; the
+    pipelined form too."""
+    from paper_1105_6040_gb300 import abi
+    s = sorters(12, 1)
+    abi.bs_set_option(s.h, "host_direct", direct)
+    try:
+        for n, p, kind in ((5000, 8, "int32"), (3000, 3, "float32"), (777, 777, "uint64"), (1 << 16, 128, "int32")):
+            x = _keys(kind, n, seed=n + p + direct)
+            want, _ = oracle.sort(x, p=p)
+            u64 = x.dtype == np.uint64
+            t = torch.from_numpy(x.view(np.int64)).view(torch.uint64) if u64 else torch.from_numpy(x)
+
+            def host(o):
+                return o.view(torch.int64).numpy().view(np.uint64) if u64 else o.numpy()
+
+            for pinned in (True, False):
+                h_in = t.pin_memory() if pinned else t.clone()
+                got = host(s.sort_keys_host(h_in, p=p))
+                assert np.array_equal(_bits(got), _bits(want)), (n, p, kind, pinned)
+            h_in = t.pin_memory()
+            h_out = torch.empty_like(h_in).pin_memory()
+            s.sort_keys_host_async(h_in, h_out, p=p)
+            s.sync()
+            assert np.array_equal(_bits(host(h_out)), _bits(want)), (n, p, kind, "async")
+    finally:
+        abi.bs_set_option(s.h, "host_direct", 1)
