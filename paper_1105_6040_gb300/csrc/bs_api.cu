@@ -700,10 +700,12 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
         if (!launch_end(h, CLS_SETUP, stream)) return BS_ERR_CUDA;
     }
 
-    // tile map: tile -> block (none when every block is in the warp length class)
+    // tile map: tile -> block (none when every block is in the warp length
+    // class: balanced blocks that short, or segments bounded by max_len; a
+    // longer segment is flagged by the plan)
     const int64_t T = int64_t(1) << g.logT;
     const int64_t ub = (n + T - 1) / T + blocks;
-    const bool no_tiles = balanced && g.wmax > 0;
+    const bool no_tiles = g.wmax > 0 && (balanced || (max_len > 0 && max_len <= g.wmax));
     g.ntiles_ub = ub;
     if (!no_tiles) {
         launch_begin(h, CLS_SETUP, stream);

@@ -217,3 +217,28 @@ def test_host_entry_points_with_short_blocks(sorters, direct):
             assert np.array_equal(_bits(host(h_out)), _bits(want)), (n, p, kind, "async")
     finally:
         abi.bs_set_option(s.h, "host_direct", 1)
+
+
+def test_segments_bounded_by_max_len_in_the_class(sorters):
+    """max_seg_len <= 1024: every segment is in the class, so the sort is the
+    plan and the class's launch alone; a segment longer than the bound is
+    reported as INVALID_ARG by the device check, as without the class."""
+    from paper_1105_6040_gb300 import abi
+    s = sorters(12, 1)
+    rng = np.random.default_rng(12)
+    lens = rng.integers(0, 1025, size=5000).astype(np.int64)
+    off = W.offsets_from_lengths(lens)
+    x = _keys("float32", int(off[-1]), seed=13)
+    want, _ = oracle.sort_segmented(x, off)
+    s.stats(reset=True)
+    got = s.sort_segmented(_dev(x), torch.from_numpy(off).cuda(), max_seg_len=1024)
+    s.sync()
+    counts, _ = s.stats(reset=True)
+    assert np.array_equal(_bits(got.cpu().numpy()), _bits(want))
+    assert counts["tile_sort"] == 1 and counts["setup"] == 1 and counts["merge"] == 0
+    bad = np.array([0, 500, 2500, 2600], dtype=np.int64)  # a 2000-key segment over the bound
+    s.sort_segmented(_dev(_keys("int32", 2600, seed=14)), torch.from_numpy(bad).cuda(), max_seg_len=1024)
+    with pytest.raises(abi.BsError) as e:
+        s.sync()
+    assert e.value.status == abi.BS_ERR_INVALID_ARG
+    s.sync()  # the error was reported once and cleared
