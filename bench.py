@@ -133,6 +133,24 @@ def traffic_from_profiles(kernel: str, workload: str):
     return None
 
 
+def instructions_from_profiles(kernel: str):
+    """Thread-instructions per key of `kernel` recorded under profiles/ by an
+    ncu capture of the current sources, or None when absent or stale."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    digest = kernel_digest()
+    pat = re.compile(r"instructions:\s*kernel=(\S+)\s+thread_instructions_per_key=([0-9.]+)\s+sources=(\w+)")
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, name)) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == kernel and m.group(3) == digest:
+                    return float(m.group(2))
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -432,6 +450,17 @@ def run_ours(args):
             kernels[cls] = {"launches_per_step": kn[cls] / kb, "ms_per_launch": avg_ms,
                             "bytes_per_launch": per_launch,
                             "gbs": per_launch / (avg_ms * 1e-3) / 1e9 if per_launch else None}
+    # the tile sort is bound by instruction issue, not HBM: its issue roofline
+    # (4 schedulers x 32 lanes per SM per clock, at the sampled SM clock)
+    ipk = instructions_from_profiles("tile_sort_kernel")
+    if "tile_sort" in kernels and ipk and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        issue_peak = sms * 4 * 32 * clk["sm_mhz"] * 1e6
+        ach = ipk * n / (kernels["tile_sort"]["ms_per_launch"] * 1e-3)
+        kernels["tile_sort"]["roofline"] = {
+            "bound": "alu", "unit": "thread-instructions/s", "achieved": ach, "peak": issue_peak,
+            "frac": ach / issue_peak, "thread_instructions_per_key": ipk,
+            "peak_source": f"issue peak: {sms} SMs x 4 schedulers x 32 lanes x {clk['sm_mhz']:g} MHz"}
     dom = max(("tile_sort", "merge"), key=lambda c: kms[c])
     achieved = kernels[dom]["gbs"]
     passes, merge_passes, merge_name = pass_counts(kernels, 2 * 4 * n)

@@ -61,3 +61,19 @@ def test_benchmark_reads_a_record_only_for_matching_device_code():
             assert got == int(nbytes)
         else:
             assert got is None or any(r[0] == kernel and r[1] == workload and r[3] == digest for r in recs)
+
+
+INSTR = re.compile(r"instructions:\s*kernel=(\S+)\s+thread_instructions_per_key=([0-9.]+)\s+sources=(\w+)")
+
+
+def test_instruction_records_parse_and_are_read_only_for_matching_code():
+    bench = _bench()
+    digest = bench.kernel_digest()
+    for name in _summaries():
+        for m in INSTR.finditer(open(os.path.join(PROFILES, name)).read()):
+            kernel, ipk, sources = m.groups()
+            assert re.fullmatch(r"[0-9a-f]{16}", sources), (name, sources)
+            assert 10.0 < float(ipk) < 1000.0, (name, ipk)
+            got = bench.instructions_from_profiles(kernel)
+            if sources == digest:
+                assert got == float(ipk)
