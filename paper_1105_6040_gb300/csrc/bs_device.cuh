@@ -418,6 +418,30 @@ __device__ __forceinline__ void seq_merge_carry(const K *sk, const uint32_t *sx,
 
 // ---------------------------------------------------------------- tile sort
 
+// A 16-byte vector of keys: N keys, element e read by get, every element
+// replaced by map.
+template <class K> struct Vec16;
+template <> struct Vec16<uint32_t> {
+    using T = uint4;
+    static constexpr int N = 4;
+    static __device__ __forceinline__ uint32_t get(const uint4 &v, int e) {
+        return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+    }
+    template <class F> static __device__ __forceinline__ void map(uint4 &v, F f) {
+        v.x = f(v.x), v.y = f(v.y), v.z = f(v.z), v.w = f(v.w);
+    }
+};
+template <> struct Vec16<uint64_t> {
+    using T = ulonglong2;
+    static constexpr int N = 2;
+    static __device__ __forceinline__ uint64_t get(const ulonglong2 &v, int e) {
+        return e == 0 ? (uint64_t)v.x : (uint64_t)v.y;
+    }
+    template <class F> static __device__ __forceinline__ void map(ulonglong2 &v, F f) {
+        v.x = f((uint64_t)v.x), v.y = f((uint64_t)v.y);
+    }
+};
+
 // Shared memory of the tile sort: codes, then (pairs) original positions and
 // values, each at a 16-byte boundary.
 // Keys alone: two ping-pong buffers of keys_round_buf(T) keys each (see
@@ -737,14 +761,27 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
             __syncthreads();  // the first round overwrites sk
             reg_sort_pairs<KPT>(k, x);
         } else {
-            // warp w loads positions [w*32*KPT, (w+1)*32*KPT), 32 consecutive
-            // keys per step; a warp past the last key holds padding alone,
-            // already in order, and skips the network and the shuffle rounds
+            // warp w loads positions [w*32*KPT, (w+1)*32*KPT): a full tile
+            // starting on a 16-byte boundary as 16-byte vectors (512 bytes per
+            // warp and step), else 32 consecutive keys per step; a warp past
+            // the last key holds padding alone, already in order, and skips
+            // the network and the shuffle rounds
             const int lane = tid & 31, w0 = (tid >> 5) * 32 * KPT;
+            using VK = Vec16<K>;
+            if (lcnt == T && ((uintptr_t)(in_k + ibase) & 15) == 0) {
 #pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                const int pos = w0 + lane + 32 * u;
-                k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
+                for (int q = 0; q < KPT / VK::N; ++q) {
+                    const typename VK::T v = *reinterpret_cast<const typename VK::T *>(
+                        in_k + ibase + w0 + VK::N * (lane + 32 * q));
+#pragma unroll
+                    for (int e = 0; e < VK::N; ++e) k[VK::N * q + e] = enc_code(VK::get(v, e), codec);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < KPT; ++u) {
+                    const int pos = w0 + lane + 32 * u;
+                    k[u] = pos < lcnt ? enc_code(in_k[ibase + pos], codec) : max_code<K>();
+                }
             }
             if (w0 < cnt) {
                 reg_sort_keys<KPT>(k);
@@ -756,13 +793,26 @@ tile_sort_kernel(Geo g, const K *__restrict__ in_k, const V *__restrict__ in_v,
 
         if constexpr (!HV) {
             // then the shared-memory rounds, and the coalesced striped store
+            // (16-byte vectors for a full tile starting on a 16-byte boundary)
             const K *res = tile_smem_rounds<K, THREADS, KPT>(k, sk, sk + keys_round_buf(T), tid, cnt);
+            using VK = Vec16<K>;
+            static_assert((keys_round_buf(T) * sizeof(K)) % 16 == 0, "both buffers 16-byte aligned");
+            if (cnt == T && ((uintptr_t)(dst_k + base) & 15) == 0) {
 #pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                const int pos = tid + u * THREADS;
-                if (pos < cnt) {
-                    const K c = res[pos];
-                    dst_k[base + pos] = fin ? dec_code(c, codec) : c;
+                for (int q = 0; q < KPT / VK::N; ++q) {
+                    const int vpos = VK::N * (tid + THREADS * q);
+                    typename VK::T v = *reinterpret_cast<const typename VK::T *>(res + vpos);
+                    if (fin) VK::map(v, [&](K c) { return dec_code(c, codec); });
+                    *reinterpret_cast<typename VK::T *>(dst_k + base + vpos) = v;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < KPT; ++u) {
+                    const int pos = tid + u * THREADS;
+                    if (pos < cnt) {
+                        const K c = res[pos];
+                        dst_k[base + pos] = fin ? dec_code(c, codec) : c;
+                    }
                 }
             }
             if (tid == 0) count_bytes(g, CLS_TILE_SORT, 2ull * sizeof(K) * cnt);
