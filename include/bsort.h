@@ -172,17 +172,18 @@ bs_status bs_sort_keys_host(bs_handle *h, const void *h_in, void *h_out, int64_t
 
 /*
  * Asynchronous host-memory sort: enqueues the copy of h_in into the input
- * buffer of one of the handle's two device slots (on an internal copy
- * stream), the sort (as bs_sort_keys: p blocks, Fig. 1; on `stream`) into
- * the slot's output buffer and the copy of the result into h_out (may equal
- * h_in; on a second internal copy stream), and returns.  Successive calls on
- * one handle form a pipeline: call k+1's copy in and call k-1's copy out run
- * on the copy engines while call k sorts, neither waiting for the other, and
- * the sorts of a handle run one after another whatever streams they are given.
- * h_in must stay unchanged and h_out unread until bs_sync_status(h), which
- * waits for all of the handle's work, returns.  The copies are asynchronous
- * only for page-locked buffers.  Device memory: four buffers of n keys
- * besides the workspace.  Errors as bs_sort_keys.
+ * buffer of one of the handle's device slots (three by default,
+ * BS_OPT_HOST_SLOTS; on an internal copy stream), the sort (as bs_sort_keys:
+ * p blocks, Fig. 1; on `stream`) into the slot's output buffer and the copy
+ * of the result into h_out (may equal h_in; on a second internal copy
+ * stream), and returns.  Successive calls on one handle form a pipeline:
+ * call k+1's copy in and call k-1's copy out run on the copy engines while
+ * call k sorts, neither waiting for the other, and the sorts of a handle run
+ * one after another whatever streams they are given.  h_in must stay
+ * unchanged and h_out unread until bs_sync_status(h), which waits for all of
+ * the handle's work, returns.  The copies are asynchronous only for
+ * page-locked buffers.  Device memory: an input and an output buffer of n
+ * keys per slot, besides the workspace.  Errors as bs_sort_keys.
  */
 bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, int64_t n,
                                   bs_dtype kt, int64_t p, void *stream);
@@ -361,12 +362,17 @@ typedef enum {
                                 are complete; it applies with the default merge consumer
                                 and keys per thread, the tree schedule and 16-byte aligned
                                 buffers.  0: one partition and one merge launch per pass */
-    BS_OPT_LENGTH_CLASSES = 12 /* 1 (default): in keys-alone sorts with the MERGE tile sort
+    BS_OPT_LENGTH_CLASSES = 12,/* 1 (default): in keys-alone sorts with the MERGE tile sort
                                 and the tree schedule, every block or segment of 1 .. 1024
                                 keys (512 at 2048-key tiles) is sorted whole by one warp
                                 inside the sort-phase launch instead of occupying a tile
                                 of its own (with at most 262,144 blocks or segments); 0:
                                 every block or segment is cut into tiles */
+    BS_OPT_HOST_SLOTS = 13   /* slots of bs_sort_keys_host_async: 3 (default, 0) or 2
+                                (two fewer device buffers of n keys; the copy out of
+                                call k-2 then gates the sort of call k).  A change
+                                first waits for the handle's work, as bs_sync_status,
+                                and returns its status */
 } bs_option;
 
 /* Sort-phase tile sorts, after the paper's three local sorts:

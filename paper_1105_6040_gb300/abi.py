@@ -260,7 +260,7 @@ def bs_set_tile_log2(h, tile_log2: int) -> None:
 OPTIONS = {"tile_log2": 0, "merge_kernel": 1, "merge_vt": 2, "wait_limit_ms": 3,
            "test_withhold": 4, "merge_schedule": 5, "local_sort": 6, "merge_tile_log2": 7,
            "merge_consumer": 8, "host_direct": 9, "count_bytes": 10,
-           "merge_persistent": 11, "length_classes": 12}
+           "merge_persistent": 11, "length_classes": 12, "host_slots": 13}
 SCHEDULES = {"tree": 0, "oddeven": 1}
 LOCAL_SORTS = {"merge": 0, "bubble": 1, "quick": 2}
 MERGE_KERNELS = {"auto": 0, "simple": 1, "tma": 2}

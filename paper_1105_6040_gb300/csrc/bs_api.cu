@@ -382,6 +382,12 @@ __global__ void tile_map_kernel(const int64_t *tprefix, int64_t S, int32_t *tseg
 
 // ====================================================================== handle
 
+// Most slots of bs_sort_keys_host_async (BS_OPT_HOST_SLOTS: 2 or 3, default
+// 3): with three the copy out of call k-3, not of call k-2, gates the sort of
+// call k, so a copy out that runs a little longer than one sort (the host
+// link shared with the copy in) does not stall the sorts.
+constexpr int HOST_SLOTS = 3;
+
 struct bs_handle {
     int device = 0;
     int sms = 1;
@@ -417,15 +423,16 @@ struct bs_handle {
     cudaStream_t own_stream = nullptr;
     void *hb = nullptr;
     size_t hb_bytes = 0;
-    // bs_sort_keys_host_async: two slots used in turn, each an input and an
-    // output device buffer; a stream for the copies in and one for the
-    // copies out, and per slot the events "copied in", "sorted", "copied out"
-    void *ab[2] = {nullptr, nullptr}, *ob[2] = {nullptr, nullptr};
-    size_t ab_bytes[2] = {0, 0}, ob_bytes[2] = {0, 0};
+    // bs_sort_keys_host_async: HOST_SLOTS slots used in turn, each an input
+    // and an output device buffer; a stream for the copies in and one for
+    // the copies out, and per slot the events "copied in", "sorted",
+    // "copied out"
+    void *ab[HOST_SLOTS] = {}, *ob[HOST_SLOTS] = {};
+    size_t ab_bytes[HOST_SLOTS] = {}, ob_bytes[HOST_SLOTS] = {};
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_sorted[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[HOST_SLOTS] = {}, ev_sorted[HOST_SLOTS] = {}, ev_out[HOST_SLOTS] = {};
     unsigned long long async_calls = 0;
+    int host_slots = HOST_SLOTS;  // slots in use (BS_OPT_HOST_SLOTS)
 };
 
 namespace {
@@ -812,7 +819,7 @@ bs_status bs_destroy(bs_handle *h) {
     if (h->d_counters) cudaFree(h->d_counters);
     if (h->d_ticket) cudaFree(h->d_ticket);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < HOST_SLOTS; ++j) {
         if (h->ab[j]) cudaFree(h->ab[j]);
         if (h->ob[j]) cudaFree(h->ob[j]);
         if (h->ev_in[j]) cudaEventDestroy(h->ev_in[j]);
@@ -1029,21 +1036,21 @@ static bs_status ensure_buf(void *&buf, size_t &have, size_t bytes) {
     return BS_OK;
 }
 
-// Call k of bs_sort_keys_host_async uses slot j = k % 2 (input buffer in_j,
-// output buffer out_j):
-//   copy-in stream:  wait "sorted"[j] (call k-2 has read in_j), copy h_in ->
+// Call k of bs_sort_keys_host_async uses slot j = k % HOST_SLOTS (input
+// buffer in_j, output buffer out_j); call k - HOST_SLOTS used it before:
+//   copy-in stream:  wait "sorted"[j] (that call has read in_j), copy h_in ->
 //                    in_j, record "copied in"[j];
-//   caller's stream: wait "copied in"[j], "copied out"[j] (call k-2's copy
-//                    out has read out_j) and "sorted"[1-j] (call k-1's sort:
-//                    the workspace is shared), sort in_j -> out_j, record
+//   caller's stream: wait "copied in"[j], "copied out"[j] (that call's copy
+//                    out has read out_j) and "sorted" of call k-1's slot (the
+//                    workspace is shared), sort in_j -> out_j, record
 //                    "sorted"[j];
 //   copy-out stream: wait "sorted"[j], copy out_j -> h_out, record
 //                    "copied out"[j].
 // So call k+1's copy in and call k-1's copy out run on the copy engines while
-// call k sorts, and neither copy waits for the other: the copy in of call
-// k+2 needs only call k's sort, not its copy out (one buffer per slot made
-// the two copies chain behind each sort).  An event not yet recorded counts
-// as complete.
+// call k sorts, and neither copy waits for the other: a slot's next copy in
+// needs only its last sort, not its copy out (one buffer per slot made the
+// two copies chain behind each sort).  An event not yet recorded counts as
+// complete.
 bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, int64_t n, bs_dtype kt,
                                   int64_t p, void *stream) {
     if (!h || n < 0 || p < 0) return BS_ERR_INVALID_ARG;
@@ -1056,13 +1063,14 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
         if (cudaStreamCreateWithFlags(&h->cp_in, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&h->cp_out, cudaStreamNonBlocking) != cudaSuccess)
             return BS_ERR_CUDA;
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < HOST_SLOTS; ++j)
             if (cudaEventCreateWithFlags(&h->ev_in[j], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->ev_sorted[j], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->ev_out[j], cudaEventDisableTiming) != cudaSuccess)
                 return BS_ERR_CUDA;
     }
-    const int j = (int)(h->async_calls & 1);
+    const int ns = h->host_slots;
+    const int j = (int)(h->async_calls % ns), prev = (j + ns - 1) % ns;
     const size_t bytes = (size_t)n * kw;
     bs_status st = ensure_buf(h->ab[j], h->ab_bytes[j], bytes);
     if (st == BS_OK) st = ensure_buf(h->ob[j], h->ob_bytes[j], bytes);
@@ -1073,7 +1081,7 @@ bs_status bs_sort_keys_host_async(bs_handle *h, const void *h_in, void *h_out, i
         cudaEventRecord(h->ev_in[j], h->cp_in) != cudaSuccess ||
         cudaStreamWaitEvent(s, h->ev_in[j], 0) != cudaSuccess ||
         cudaStreamWaitEvent(s, h->ev_out[j], 0) != cudaSuccess ||
-        cudaStreamWaitEvent(s, h->ev_sorted[1 - j], 0) != cudaSuccess)
+        cudaStreamWaitEvent(s, h->ev_sorted[prev], 0) != cudaSuccess)
         return BS_ERR_CUDA;
     st = bs_sort_keys(h, h->ab[j], h->ob[j], n, kt, p, (void *)s);
     if (st != BS_OK) return st;
@@ -1358,6 +1366,18 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
         h->length_classes = (int)value;
         return BS_OK;
+    case BS_OPT_HOST_SLOTS: {
+        if (value != 0 && value != 2 && value != 3) return BS_ERR_INVALID_ARG;
+        const int v = value ? (int)value : HOST_SLOTS;
+        if (v != h->host_slots) {
+            // the slot sequence restarts: wait for the calls in flight first
+            const bs_status st = bs_sync_status(h);
+            h->host_slots = v;
+            h->async_calls = 0;
+            return st;
+        }
+        return BS_OK;
+    }
     default:
         return BS_ERR_INVALID_ARG;
     }

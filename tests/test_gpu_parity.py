@@ -315,15 +315,19 @@ def test_host_entry_direct_and_copy(direct, case):
         s.close()
 
 
-def test_host_async_pipeline():
+@pytest.mark.parametrize("slots", [3, 2])
+def test_host_async_pipeline(slots):
     """bs_sort_keys_host_async: six calls in flight on one handle (its two
-    slots of input and output buffers used in turn, copies overlapping
-    sorts), interleaved with
+    or three slots of input and output buffers used in turn, copies
+    overlapping sorts), interleaved with
     calls on a second handle and stream; int32, float32 and uint64 keys,
     growing sizes (a buffer regrown between calls), one call in place and
     one from pageable memory.  Every result is the oracle's."""
+    from paper_1105_6040_gb300 import abi
     from paper_1105_6040_gb300.abi import Sorter
     sorters = [Sorter(0), Sorter(0)]
+    for sr in sorters:
+        abi.bs_set_option(sr.h, "host_slots", slots)
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     try:
         xs = [W.uniform_int32((1 << 21) + 13, 111), W.normal_float32_edges(1 << 22, 112),
