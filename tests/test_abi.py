@@ -82,3 +82,20 @@ def test_workspace_is_one_scratch_copy_plus_small_index_arrays():
     steps = [abi.bs_workspace_bytes(int(2.5e6 + 5e5 * i), 2, "int32") for i in range(6)]
     diffs = np.diff(steps)
     assert diffs.max() - diffs.min() <= 1024
+
+
+def _enum(src, prefix):
+    return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b({prefix}\w+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_tables_match_the_header_enums():
+    """The binding's option, dtype and status numbers are the header's."""
+    src = open(os.path.join(ROOT, "include", "bsort.h")).read()
+    opts = _enum(src, "BS_OPT_")
+    assert {("BS_OPT_" + k.upper()): v for k, v in abi.OPTIONS.items()} == opts
+    dts = {k: v for k, v in _enum(src, "BS_").items()
+           if k in ("BS_NONE", "BS_INT32", "BS_UINT32", "BS_FLOAT32", "BS_INT64", "BS_UINT64", "BS_FLOAT64")}
+    assert {("BS_" + k.upper()): v for k, v in abi.DTYPES.items()} == dts
+    for name in ("BS_OK", "BS_ERR_INVALID_ARG", "BS_ERR_UNSUPPORTED_DTYPE", "BS_ERR_OUT_OF_MEMORY",
+                 "BS_ERR_CUDA", "BS_ERR_TIMEOUT"):
+        assert getattr(abi, name) == _enum(src, "BS_")[name], name
