@@ -355,13 +355,16 @@ typedef enum {
                                 handle's counters (one atomic per tile), which
                                 bs_launch_stats reports; 0 (default): nothing is counted
                                 and `bytes` stays at what earlier counted sorts added */
-    BS_OPT_MERGE_PERSISTENT = 11,/* 1 (default): every merge pass of a sort (the in-block
-                                levels and the merge phase's rounds) runs in ONE persistent
-                                launch whose CTAs take merge tiles from a work queue in
-                                device memory, each tile starting once the runs it reads
-                                are complete; it applies with the default merge consumer
-                                and keys per thread, the tree schedule and 16-byte aligned
-                                buffers.  0: one partition and one merge launch per pass */
+    BS_OPT_MERGE_PERSISTENT = 11,/* every merge pass of a sort (the in-block levels and
+                                the merge phase's rounds) in ONE persistent launch whose
+                                CTAs take merge tiles from a work queue in device memory,
+                                each tile starting once the runs it reads are complete:
+                                1 (default) when a level holds a batch of tiles for every
+                                resident CTA (from about 2^25 keys at 8192-key merge
+                                tiles; smaller sorts run faster per pass), 2 always, 0
+                                never (one partition and one merge launch per pass).  It
+                                applies with the default merge consumer and keys per
+                                thread, the tree schedule and 16-byte aligned buffers */
     BS_OPT_LENGTH_CLASSES = 12,/* 1 (default): in keys-alone sorts with the MERGE tile sort
                                 and the tree schedule, every block or segment of 1 .. 1024
                                 keys (512 at 2048-key tiles) is sorted whole by one warp

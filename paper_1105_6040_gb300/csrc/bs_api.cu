@@ -408,7 +408,8 @@ struct bs_handle {
     int merge_consumer = 0;   // 0 per-thread sequential merge, 1 warp bitonic merger
     int host_direct = 1;      // bs_sort_keys_host: address page-locked host buffers directly
     int count_bytes = 0;      // kernels count algorithmic bytes (BS_OPT_COUNT_BYTES)
-    int persistent = 1;       // every merge level in one persistent launch (BS_OPT_MERGE_PERSISTENT)
+    int persistent = 1;       // every merge level in one persistent launch: 1 when large enough,
+                              // 2 always, 0 never (BS_OPT_MERGE_PERSISTENT)
     int length_classes = 1;   // warp length class for short segments (BS_OPT_LENGTH_CLASSES)
     cudaStream_t last_stream = nullptr;
     // per-launch timing
@@ -748,7 +749,7 @@ bs_status do_sort(bs_handle *h, const void *kin, void *kout, const void *vin, vo
     a.local_sort = h->local_sort;
     a.merge_tile_log2 = h->merge_tile_log2;
     a.merge_consumer = h->merge_consumer;
-    a.persistent = persist && pwords <= W.pcnt_words;
+    a.persistent = (persist && pwords <= W.pcnt_words) ? h->persistent : 0;
     a.pcnt = (unsigned *)(ws + W.pcnt);
     a.pcnt_words = pwords;
     a.no_tiles = no_tiles;
@@ -1001,7 +1002,7 @@ bs_status bs_merge_runs(bs_handle *h, const void *d_kin, void *d_kout, const voi
     a.local_sort = 0;
     a.merge_tile_log2 = h->merge_tile_log2;
     a.merge_consumer = h->merge_consumer;
-    a.persistent = persist;
+    a.persistent = persist ? h->persistent : 0;
     a.pcnt = (unsigned *)(ws + W.pcnt);
     a.pcnt_words = pwords;
     return kw == 4 ? run_passes_u32(a, L) : run_passes_u64(a, L);
@@ -1359,7 +1360,7 @@ bs_status bs_set_option(bs_handle *h, bs_option opt, int64_t value) {
         h->count_bytes = (int)value;
         return BS_OK;
     case BS_OPT_MERGE_PERSISTENT:
-        if (value != 0 && value != 1) return BS_ERR_INVALID_ARG;
+        if (value < 0 || value > 2) return BS_ERR_INVALID_ARG;
         h->persistent = (int)value;
         return BS_OK;
     case BS_OPT_LENGTH_CLASSES:

@@ -59,7 +59,8 @@ struct PassArgs {
     int local_sort;           // tile sort: 0 network + merges, 1 bubble (Fig. 2), 2 quick (Fig. 4)
     int merge_tile_log2;      // merge-pass tile (0: the sort tile; else 11 .. logT)
     int merge_consumer;       // TMA merge consumers: 0 per-thread sequential merge, 1 warp bitonic
-    int persistent;           // 1: every merge level in one persistent launch where it can run
+    int persistent;           // every merge level in one persistent launch where it can run:
+                              // 1 when a level holds a batch for every resident CTA, 2 always
     unsigned *pcnt;           // its pair counters and work queue (zeroed before the sort phase)
     int64_t pcnt_words;       // capacity of pcnt in 32-bit words
     bool no_tiles;            // every block is in the warp length class: no tile sort launch

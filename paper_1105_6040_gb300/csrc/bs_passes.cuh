@@ -180,6 +180,14 @@ int launch_merge_persist_at(const PassArgs &a, Launcher &L, const PersistPlan &P
     }
     if (occ.load() <= 0) return 0;
     if (a.merge_impl == MERGE_AUTO && smem > TMA_SMEM_AUTO_LIMIT) return 0;
+    // A level is handed out as batches of PERSIST_BATCH tiles, each merged by
+    // one CTA tile after tile, while the per-pass kernels merge every tile of
+    // a level at once: unless a level holds a batch for every resident CTA,
+    // the levels' chain of batches is slower than the per-pass launches
+    // (2^20 int32 keys, p = 2: 0.33 against 0.10 ms; 2^24: 0.80 against
+    // 0.56; 2^26: 1.74 against 1.87).  a.persistent == 2 forces it.
+    const int64_t level_tiles = (a.g.n + (int64_t(1) << P.mlogT) - 1) >> P.mlogT;
+    if (a.persistent != 2 && level_tiles < (int64_t)L.sms * occ.load() * PERSIST_BATCH) return 0;
     // every resident CTA (the queue balances the work), no more than there are batches
     const int64_t grid = grid_for(batches, (int64_t)L.sms * occ.load());
     PersistPlan Pm = P;

@@ -199,6 +199,31 @@ class GpuExecutor:
             self.reserved_bytes += bs_reserve_workspace(sorter.h, res_n, res_s, "int32")
             self.slots.append({"stream": torch.cuda.Stream(self.dev), "sorter": sorter, "busy": None})
         self.start_event = None
+        self._warm_up()
+
+    def _warm_up(self):
+        """Run each slot once through every path a request can take (a lone
+        request of each size class, a gathered batch), so that no request
+        pays for loading the library's kernels on their first use."""
+        t, cfg = self.torch, self.cfg
+        pool = self.pools["int32"]
+        sizes, n = [], max(cfg.lo, 1)
+        while n <= min(cfg.hi, pool.numel()):
+            sizes.append(n)
+            n *= 4
+        for slot in self.slots:
+            st, sorter = slot["stream"], slot["sorter"]
+            with t.cuda.stream(st):
+                for n in sizes:
+                    sorter.sort_keys(pool[:n], p=1, stream=st)
+                k = min(cfg.batch_max_reqs, 8)
+                lens = np.full(k, max(1, min(cfg.small_max, cfg.batch_max_keys // k)), dtype=np.int64)
+                off = W.offsets_from_lengths(lens)
+                src = np.zeros(k, dtype=np.int64)
+                sorter.sort_gathered(pool, t.from_numpy(src).to(self.dev), t.from_numpy(off).to(self.dev),
+                                     max_seg_len=int(lens.max()), stream=st)
+            sorter.sync()
+        t.cuda.synchronize()
 
     # -- executor interface
     def start(self, clock):

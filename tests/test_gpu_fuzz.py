@@ -2,7 +2,8 @@
 pairs, segmented keys or pairs, gathered segments), a key type and, for
 pairs, a value type, a size (0 to 2^20, log-uniform, tile edges favoured),
 p, the sort tile, and the library options that pick code paths (warp length
-class, persistent or per-pass merge, merge tile), and compares the result
+class, the merge path -- persistent forced, by size, or per pass --, merge
+tile), and compares the result
 with the oracle bit for bit.  The options are set on one handle and reset
 between cases, so the cases also check that a handle carries no state from
 one configuration to the next."""
@@ -112,7 +113,7 @@ def test_random_case_matches_oracle(handles, case):
     vk = VAL_KINDS[int(rng.integers(len(VAL_KINDS)))]
     tile = int(rng.integers(11, 14))
     s = handles(tile)
-    opts = {"length_classes": int(rng.integers(2)), "merge_persistent": int(rng.integers(2)),
+    opts = {"length_classes": int(rng.integers(2)), "merge_persistent": int(rng.integers(3)),
             "merge_tile_log2": int(rng.choice([0, 11, tile]))}
     for name, v in opts.items():
         abi.bs_set_option(s.h, name, v)

@@ -141,7 +141,7 @@ def test_gathered_short_segments(sorters):
 
 @pytest.mark.parametrize("n,p", [(5000, 8), (5120, 5), (5125, 5), (1 << 20, 4096), (100, 100),
                                  (7, 3), (300001, 1000)])
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [2, 0])
 def test_balanced_short_blocks(sorters, n, p, persistent):
     """Balanced blocks short enough for the class (n/p up to 1024): the
     cross-block rounds merge the class's output; 5125/5 = 1025 is one key

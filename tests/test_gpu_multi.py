@@ -75,12 +75,15 @@ def test_exchange_sort_one_rank_on_gpu(sorter):
 def test_unsorted_runs_and_overlapping_offsets_stay_in_bounds(sorter):
     """Inputs that break the sortedness a merge pass relies on (runs that are
     not sorted; overlapping segment offsets spanning many tiles) give an
-    undefined output but no fault, and the handle keeps working."""
+    undefined output but no fault, and the handle keeps working: the
+    persistent merge (forced at this size), the per-pass TMA merge and the
+    plain merge kernel."""
     from paper_1105_6040_gb300 import abi
     x = W.uniform_int32(1 << 18, seed=11)
     d = torch.from_numpy(x).cuda()
-    for tma in ("tma", "simple"):
+    for tma, persistent in (("tma", 2), ("tma", 0), ("simple", 0)):
         abi.bs_set_option(sorter.h, "merge_kernel", tma)
+        abi.bs_set_option(sorter.h, "merge_persistent", persistent)
         sorter.merge_runs(d, [0, 100003, 150000, 1 << 18])  # runs not sorted
         sorter.sync()
         bad = torch.tensor([0, 150000, 50000, 1 << 18], dtype=torch.int64, device="cuda")
@@ -90,6 +93,7 @@ def test_unsorted_runs_and_overlapping_offsets_stay_in_bounds(sorter):
         sorter.sync()
         assert np.array_equal(out.cpu().numpy(), np.sort(x))
     abi.bs_set_option(sorter.h, "merge_kernel", "auto")
+    abi.bs_set_option(sorter.h, "merge_persistent", 1)
 
 
 def _gpu_exchange_worker(rank, world, port, sizes, kind, q):

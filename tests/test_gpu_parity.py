@@ -368,11 +368,13 @@ def test_invalid_args(sorter):
 
 def test_launch_stats_count_passes(sorter):
     """1 tile-sort pass + 7 in-block levels (2^19 / 4096 = 2^7 tiles) + 1 cross
-    round: one persistent merge launch by default, 8 partition + 8 merge
-    launches per pass otherwise; the algorithmic bytes are the same."""
+    round: one persistent merge launch when forced, 8 partition + 8 merge
+    launches per pass otherwise -- and by default at this size, too small
+    for every resident CTA to get a batch of a level; the algorithmic bytes
+    are the same."""
     from paper_1105_6040_gb300 import abi
     n = 1 << 20
-    for persistent, merges, parts in ((1, 1, 0), (0, 8, 8)):
+    for persistent, merges, parts in ((2, 1, 0), (0, 8, 8), (1, 8, 8)):
         abi.bs_set_option(sorter.h, "merge_persistent", persistent)
         sorter.stats(reset=True)
         abi.bs_set_option(sorter.h, "count_bytes", 1)
@@ -387,7 +389,7 @@ def test_launch_stats_count_passes(sorter):
     # counting off (the default): the same sort adds no bytes
     sorter.sort_keys(_to_dev(W.uniform_int32(n, 92)), p=2)
     counts, byts = sorter.stats(reset=True)
-    assert counts["merge"] == 1 and byts["tile_sort"] == 0 and byts["merge"] == 0
+    assert counts["merge"] == 8 and byts["tile_sort"] == 0 and byts["merge"] == 0
 
 
 @pytest.mark.parametrize("tile_log2,merge_tile_log2", [(12, 0), (13, 11), (11, 11), (13, 13)])
@@ -402,6 +404,7 @@ def test_persistent_merge_matches_per_pass_and_oracle(tile_log2, merge_tile_log2
     per = Sorter(0, tile_log2=tile_log2, merge_tile_log2=merge_tile_log2)
     abi.bs_set_option(per.h, "merge_persistent", 0)
     pst = Sorter(0, tile_log2=tile_log2, merge_tile_log2=merge_tile_log2)
+    abi.bs_set_option(pst.h, "merge_persistent", 2)  # these sizes would run per pass by default
     try:
         for n, p in ((1, 1), (T - 1, 1), (3 * T + 7, 2), (100003, 3), (1 << 18, 6), (262139, 4096),
                      ((1 << 20) + 5, 7), (1 << 21, 1)):
@@ -595,7 +598,7 @@ def test_unaligned_buffers_fall_back(sorter):
 
 # ------------------------------------------------------------------ failure detection
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [2, 0])
 def test_bounded_wait_runs_out_and_reports_timeout(persistent):
     """A stage that nothing fills: the merge's bounded waits run out (in the
     persistent merge, the other CTAs' waits on the pairs that CTA never

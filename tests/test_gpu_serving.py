@@ -68,8 +68,8 @@ def test_gathered_segments_match_oracle():
 
 
 def test_tight_memory_cap_defers_and_is_respected():
-    """Admission by memory: with a cap of three largest launches' outputs and
-    requests arriving ten times faster, launches are deferred, the bytes in
+    """Admission by memory: with a cap of about one largest launch's output and
+    requests arriving twenty times faster, launches are deferred, the bytes in
     flight never exceed the cap, the handles' scratch reserved at start-up is
     all the library uses (it does not grow during the run), batching engages,
     and every result is still the request sorted alone."""
@@ -78,8 +78,10 @@ def test_tight_memory_cap_defers_and_is_respected():
     from paper_1105_6040_gb300 import serving as S
     from paper_1105_6040_gb300.abi import Sorter
 
-    cap = 3 * 4 * (1 << 16)
-    cfg = S.ServingConfig(rate=20000, duration=0.1, lo=1 << 10, hi=1 << 16, small_max=1 << 12,
+    # room for one largest launch (2^16 int32 keys and its batch scratch) and
+    # little more: a second launch in flight beside any sizeable one waits
+    cap = 4 * (1 << 16) + 4096
+    cfg = S.ServingConfig(rate=40000, duration=0.1, lo=1 << 10, hi=1 << 16, small_max=1 << 12,
                           batch_max_keys=1 << 16, batch_max_reqs=64, streams=4,
                           pool_keys=1 << 18, mem_cap_bytes=cap, keep_results=True)
     summary, reqs, ex = S.serve(cfg)
